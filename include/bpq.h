@@ -1,0 +1,244 @@
+/*
+ * bpq.h — C ABI of a GB300 (sm_103a) implementation of the query-time path of
+ * bilayer product-quantization search: Babenko & Lempitsky, "Improving Bilayer
+ * Product Quantization for Billion-Scale Approximate Nearest Neighbors in High
+ * Dimensions" (arXiv:1404.1831).
+ *
+ * Notation (the paper's): D dimensions, split into two halves of D/2; coarse
+ * codebooks C^1, C^2 of T codewords each define T*T cells W_ij (Eq. 4); every
+ * point stores its cell and an M-byte PQ code of its displacement from the cell
+ * centroid (Eqs. 6-7), with K = 256 codewords per sub-quantizer.  The PQ split is
+ * aligned with the halves: M even, D/M divides D/2.
+ *
+ * Conventions for every entry point:
+ *  - Every call returns int: BPQ_OK (0) or a negative BPQ_E* code; the message
+ *    of the last failure on the calling thread is bpq_last_error().  No C++
+ *    exception crosses this boundary.
+ *  - Pointers named *_dev are device pointers on the index's device; *_host are
+ *    host pointers.  The caller owns every buffer it passes and the library
+ *    never frees them.  The index owns its codebooks, tables and lists.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  It is borrowed; work is enqueued on it and nothing synchronizes
+ *    unless the entry point says so.
+ *  - Matrices are row-major and dense: n x D float32 points/queries, etc.
+ *  - Point ids are int32 >= 0; -1 marks an empty result slot.
+ */
+#ifndef BPQ_H_
+#define BPQ_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+enum {
+  BPQ_OK = 0,
+  BPQ_EINVAL = -1,     /* invalid argument (null pointer, bad size, bad id, ...) */
+  BPQ_ENOMEM = -2,     /* device or host allocation failed */
+  BPQ_EIO = -3,        /* file could not be read or written */
+  BPQ_ECORRUPT = -4,   /* index file failed its header or checksum test */
+  BPQ_ETIMEOUT = -5,   /* a bounded device wait gave up */
+  BPQ_ECUDA = -6,      /* a CUDA runtime call failed */
+  BPQ_ECAPACITY = -7,  /* a fixed-size buffer (workspace, band, output) is too small */
+  BPQ_ESTATE = -8      /* call out of order (e.g. search before bpq_finalize) */
+};
+
+/* Codebook variants. */
+enum {
+  BPQ_VARIANT_GLOBAL = 0, /* Multi-D-ADC codebooks: global R_1..R_M (§2.3.1); FBPQ and
+                             reconstruction scoring */
+  BPQ_VARIANT_LOCAL = 1   /* HBPQ: per-half-cell local codebooks Q^i_k, S^j_k (§3.2) */
+};
+
+/* Candidate scorers. */
+enum {
+  BPQ_SCORER_FBPQ = 0,  /* Eq. 8 with Eq. 9: per-query lookup tables reused in every
+                           cell, O(M) per candidate (§3.1) */
+  BPQ_SCORER_RECON = 1, /* Multi-D-ADC: per-cell query displacement and explicit
+                           reconstruction, O(D) per candidate (§2.3.3) */
+  BPQ_SCORER_HBPQ = 2   /* HBPQ: reconstruction with local codebooks, O(D) (§3.2) */
+};
+
+typedef struct bpq_index bpq_index;
+
+typedef struct {
+  int32_t D;            /* dimensionality; even */
+  int32_t T;            /* coarse codewords per half, 1..4096 (T*T cells) */
+  int32_t M;            /* PQ sub-quantizers; even, D/M must divide D/2, M*256 <= 8192 */
+  int32_t ksub;         /* codewords per PQ codebook; must be 256 (one byte per index) */
+  int32_t variant;      /* BPQ_VARIANT_* */
+  int32_t kmeans_iters; /* Lloyd iterations for bpq_train_load */
+} bpq_params;
+
+typedef struct {
+  int64_t n_points;        /* points in the finalized lists */
+  int64_t n_pending;       /* points added since the last bpq_finalize */
+  int64_t n_nonempty;      /* non-empty cells of the finalized lists */
+  int64_t max_cell;        /* largest cell population */
+  int64_t device_bytes;    /* device memory the index holds */
+  bpq_params params;
+} bpq_info;
+
+/* Read-only device views of the index arrays (valid until the next mutating call). */
+typedef struct {
+  const float* C1;      /* T x D/2 */
+  const float* C2;      /* T x D/2 */
+  const float* R;       /* M x 256 x D/M (global variant) */
+  const float* Q;       /* T x M/2 x 256 x D/M (local variant, else NULL) */
+  const float* S;       /* T x M/2 x 256 x D/M (local variant, else NULL) */
+  const float* X1;      /* T x M/2 x 256: 2<c^1_i block k, R_k[t]>, k < M/2 (Eq. 9) */
+  const float* X2;      /* T x M/2 x 256: 2<c^2_j block k, R_{M/2+k}[t]> (Eq. 9) */
+  const uint32_t* offsets; /* T*T + 1 start positions of the cells (§2.3.2) */
+  const uint8_t* codes; /* n_points x M, cell-contiguous */
+  const int32_t* ids;   /* n_points, ascending inside each cell */
+} bpq_arrays;
+
+/* One visited cell, as bpq_traverse writes it. */
+typedef struct {
+  uint32_t cell;   /* i*T + j */
+  uint32_t begin;  /* first list position of the cell */
+  uint32_t count;  /* points of the cell (> 0) */
+  float key;       /* d1[i] + d2[j] in FP32 */
+} bpq_cell;
+
+/* Text of the last error on the calling thread ("" if none). */
+const char* bpq_last_error(void);
+
+/*
+ * bpq_create — index from given codebooks (copied from host memory).
+ *  C1_host, C2_host: T x D/2 coarse codebooks C^1, C^2 (§2.3.1).
+ *  R_host: M x 256 x D/M residual codebooks R_1..R_M (§2.3.1); required for both
+ *          variants (the local variant uses it only as its global fallback).
+ *  Q_host, S_host: T x M/2 x 256 x D/M local codebooks Q^i_k, S^j_k (§3.2, Eq. 11);
+ *          required for BPQ_VARIANT_LOCAL, ignored otherwise.
+ * Builds the query-independent FBPQ tables X1, X2 (Eq. 9, §3.3) on the device.
+ * Errors: BPQ_EINVAL for a bad shape or null pointer, BPQ_ENOMEM, BPQ_ECUDA.
+ */
+int bpq_create(bpq_index** out, const bpq_params* p, const float* C1_host, const float* C2_host,
+               const float* R_host, const float* Q_host, const float* S_host, int device);
+
+/*
+ * bpq_train_load — train a new index on the GPU, or load one from a file.
+ *  If learn_dev != NULL: learns C^1, C^2 by K-means on the point halves, then
+ *  R_1..R_M by K-means on the displacements from the cell centroids (§2.3.1),
+ *  and for BPQ_VARIANT_LOCAL the local codebooks of every half-cell (§3.2,
+ *  Eqs. 10-11).  learn_dev: n_learn x D float32, device, integer-valued in
+ *  [-2^20, 2^20] (K-means sums are exact int64 and every centroid is the mean
+ *  rounded half up to an integer); n_learn >= max(T, 256).  K-means starts from
+ *  the first T (or 256) learn vectors; local codebooks start from the global ones.
+ *  Synchronizes the stream before returning.
+ *  Otherwise loads path (written by bpq_save) onto `device`.
+ * Errors: BPQ_EINVAL (bad params, non-integer data), BPQ_EIO, BPQ_ECORRUPT,
+ *         BPQ_ENOMEM, BPQ_ECUDA.
+ */
+int bpq_train_load(bpq_index** out, const bpq_params* p, const float* learn_dev, int64_t n_learn,
+                   const char* path, int device, void* stream);
+
+/*
+ * bpq_encode — cell and PQ code of n points (§2.3.2, Eqs. 6-7; HBPQ Eq. 12),
+ * without adding them.  x_dev: n x D float32.  cell_out_dev: n int32 (i*T + j).
+ * codes_out_dev: n x M uint8.  Ties go to the lowest codeword index.
+ */
+int bpq_encode(const bpq_index* idx, const float* x_dev, int64_t n, int32_t* cell_out_dev,
+               uint8_t* codes_out_dev, void* stream);
+
+/*
+ * bpq_add — encode n points and append them to the pending set.  ids_dev: n
+ * int32 >= 0 (NULL = consecutive ids starting at the number of points added so
+ * far).  The points become searchable after bpq_finalize.  Total points < 2^32.
+ */
+int bpq_add(bpq_index* idx, const float* x_dev, int64_t n, const int32_t* ids_dev, void* stream);
+
+/*
+ * bpq_finalize — build the inverted multi-index lists (§2.3.2): all points of a
+ * cell contiguous, cells in id order, ids ascending inside a cell, plus the
+ * T*T + 1 cell start offsets.  Merges pending points into existing lists.
+ * Synchronizes the stream before returning.
+ */
+int bpq_finalize(bpq_index* idx, void* stream);
+
+/*
+ * bpq_query_tables — per-query tables of §3.1 for nq queries (queries_dev:
+ * nq x D float32): d1_dev, d2_dev: nq x T squared distances ||q^1 - c^1_i||^2,
+ * ||q^2 - c^2_j||^2 (Eqs. 2-3); lut_dev (may be NULL): nq x M x 256 entries
+ * ||R_k[t]||^2 - 2<q_k, R_k[t]> (the query terms of Eq. 8 with the codeword norms
+ * of Eq. 9).
+ */
+int bpq_query_tables(const bpq_index* idx, const float* queries_dev, int64_t nq, float* d1_dev,
+                     float* d2_dev, float* lut_dev, void* stream);
+
+/*
+ * Candidate budgets: L_host points to nq int64 values (L_stride == 1) or to one
+ * value used for every query (L_stride == 0); every L must be in [1, 2^31).
+ */
+
+/* Device workspace bytes bpq_search / bpq_traverse need for nq queries at budget <= L_max. */
+size_t bpq_search_workspace_size(const bpq_index* idx, int64_t nq, int64_t L_max, int32_t k,
+                                 int32_t scorer);
+
+/*
+ * bpq_traverse — visit order of the inverted multi-index (§2.3.3): for each query,
+ * the non-empty cells in non-decreasing d1[i] + d2[j] order, ties by cell id,
+ * up to and including the first cell at which the visited points reach L (the
+ * multi-sequence stopping rule; all cells if the index holds fewer points).
+ * Empty cells consume order but hold no candidates, so they are not listed.
+ *  cells_dev: nq x cap bpq_cell; ncells_dev: nq int32; npoints_dev: nq int64 (L').
+ *  If a query visits more than cap non-empty cells its ncells is -1.
+ *  workspace: bpq_search_workspace_size(idx, nq, max L, 1, BPQ_SCORER_FBPQ) bytes.
+ */
+int bpq_traverse(const bpq_index* idx, const float* queries_dev, int64_t nq, const int64_t* L_host,
+                 int64_t L_stride, int32_t cap, bpq_cell* cells_dev, int32_t* ncells_dev,
+                 int64_t* npoints_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/*
+ * bpq_search — approximate k-NN (§2.3.3, §3.1, §3.2): for each query, the k
+ * candidates of the visited cells with the smallest squared distance
+ * ||q - x^||^2 (Eq. 8), ascending, ties by id; slots beyond the candidate count
+ * hold id -1 and distance +inf.
+ *  queries_dev: nq x D float32; k in [1, 1024]; scorer: BPQ_SCORER_*
+ *  (FBPQ and RECON need the global variant, HBPQ the local one).
+ *  ids_dev: nq x k int32; dists_dev: nq x k float32.
+ *  workspace_dev: at least bpq_search_workspace_size(idx, nq, max L, k, scorer)
+ *  bytes, or fewer: queries are then processed in chunks that fit (at least one
+ *  query must fit, else BPQ_ECAPACITY).
+ * Asynchronous on stream; per-query failures of a fixed-size buffer (a cell tie
+ * group larger than the traversal band) are reported by bpq_search_status.
+ */
+int bpq_search(const bpq_index* idx, const float* queries_dev, int64_t nq, const int64_t* L_host,
+               int64_t L_stride, int32_t k, int32_t scorer, int32_t* ids_dev, float* dists_dev,
+               void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/*
+ * bpq_search_status — synchronizes the stream and returns BPQ_OK, or
+ * BPQ_ECAPACITY if any query of the last bpq_search / bpq_traverse on this
+ * workspace overflowed a fixed-size buffer.
+ */
+int bpq_search_status(const bpq_index* idx, void* workspace_dev, void* stream);
+
+/*
+ * bpq_search_host — bpq_search with host buffers: copies queries_host (nq x D
+ * float32) to the device, searches with a workspace the index owns, copies the
+ * results to ids_host / dists_host (nq x k) and synchronizes the stream.
+ */
+int bpq_search_host(bpq_index* idx, const float* queries_host, int64_t nq, const int64_t* L_host,
+                    int64_t L_stride, int32_t k, int32_t scorer, int32_t* ids_host,
+                    float* dists_host, void* stream);
+
+/* bpq_info / bpq_arrays — sizes and read-only device views (see the structs). */
+int bpq_get_info(const bpq_index* idx, bpq_info* out);
+int bpq_get_arrays(const bpq_index* idx, bpq_arrays* out);
+
+/* bpq_save — write codebooks, lists and a checksummed header to path (synchronizes). */
+int bpq_save(const bpq_index* idx, const char* path);
+
+/* bpq_free — release the index and its device memory (NULL is allowed). */
+void bpq_free(bpq_index* idx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPQ_H_ */

@@ -1,0 +1,305 @@
+"""Python binding of libbpq, the GB300 (sm_103a) bilayer product-quantization search library.
+
+Argument marshalling only: every step of training, encoding, traversal and
+scoring runs in the CUDA kernels behind the C ABI of ``include/bpq.h``.  PyTorch
+provides device memory and streams.  There is no CPU fallback: if
+``libbpq.so`` is missing, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+BPQ_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "EIO", -4: "ECORRUPT", -5: "ETIMEOUT", -6: "ECUDA", -7: "ECAPACITY",
+          -8: "ESTATE"}
+VARIANT_GLOBAL, VARIANT_LOCAL = 0, 1
+SCORERS = {"fbpq": 0, "recon": 1, "hbpq": 2}
+
+
+class BpqError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_int32), ("T", ctypes.c_int32), ("M", ctypes.c_int32), ("ksub", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("kmeans_iters", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_pending", ctypes.c_int64), ("n_nonempty", ctypes.c_int64),
+                ("max_cell", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("params", Params)]
+
+
+class Arrays(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("C1", "C2", "R", "Q", "S", "X1", "X2", "offsets", "codes", "ids")]
+
+
+CELL_DTYPE = np.dtype([("cell", "<u4"), ("begin", "<u4"), ("count", "<u4"), ("key", "<f4")])
+
+# Every entry point of include/bpq.h, with its ctypes signature.
+_P = ctypes.c_void_p
+_SIGS = {
+    "bpq_last_error": (ctypes.c_char_p, []),
+    "bpq_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(Params), _P, _P, _P, _P, _P, ctypes.c_int]),
+    "bpq_train_load": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(Params), _P, ctypes.c_int64,
+                                      ctypes.c_char_p, ctypes.c_int, _P]),
+    "bpq_encode": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
+    "bpq_add": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    "bpq_finalize": (ctypes.c_int, [_P, _P]),
+    "bpq_query_tables": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P]),
+    "bpq_search_workspace_size": (ctypes.c_size_t, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                                    ctypes.c_int32]),
+    "bpq_traverse": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P,
+                                    ctypes.c_size_t, _P]),
+    "bpq_search": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P,
+                                  _P, _P, ctypes.c_size_t, _P]),
+    "bpq_search_status": (ctypes.c_int, [_P, _P, _P]),
+    "bpq_search_host": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                       _P, _P, _P]),
+    "bpq_get_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    "bpq_get_arrays": (ctypes.c_int, [_P, ctypes.POINTER(Arrays)]),
+    "bpq_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "bpq_free": (None, [_P]),
+}
+
+_LIB = None
+
+
+def library_path():
+    return os.path.join(HERE, "libbpq.so")
+
+
+def lib():
+    """The loaded libbpq.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "(the CUDA library is required; there is no CPU fallback)")
+        so = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(so, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = so
+    return _LIB
+
+
+def _check(rc):
+    if rc != BPQ_OK:
+        raise BpqError(rc, lib().bpq_last_error().decode())
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _L_array(L, nq):
+    L = np.asarray(L, dtype=np.int64)
+    if L.ndim == 0:
+        return np.ascontiguousarray(L.reshape(1)), 0
+    if L.shape != (nq,):
+        raise ValueError("L must be a scalar or have one value per query")
+    return np.ascontiguousarray(L), 1
+
+
+class _CudaView:
+    """Wraps a raw device pointer for torch.as_tensor (CUDA array interface)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), True),
+                                         "version": 2}
+
+
+class Index:
+    """An inverted multi-index with PQ-coded displacements on one GPU."""
+
+    def __init__(self, handle, device=0):
+        self._h = handle
+        self.device = device
+        self._ws = None
+
+    # -- construction ---------------------------------------------------------
+    @staticmethod
+    def _params(D, T, M, variant, iters):
+        return Params(D=D, T=T, M=M, ksub=256, variant=variant, kmeans_iters=iters)
+
+    @classmethod
+    def create(cls, C1, C2, R, Q=None, S=None, device=0):
+        """Index from host codebooks: C1, C2 (T, D/2); R (M, 256, D/M); Q, S (T, M/2, 256, D/M) for HBPQ."""
+        C1 = np.ascontiguousarray(C1, dtype=np.float32)
+        C2 = np.ascontiguousarray(C2, dtype=np.float32)
+        R = np.ascontiguousarray(R, dtype=np.float32)
+        T, h = C1.shape
+        M = R.shape[0]
+        variant = VARIANT_LOCAL if Q is not None else VARIANT_GLOBAL
+        p = cls._params(2 * h, T, M, variant, 0)
+        qs = [np.ascontiguousarray(a, dtype=np.float32) if a is not None else None for a in (Q, S)]
+        h_out = ctypes.c_void_p()
+        _check(lib().bpq_create(ctypes.byref(h_out), ctypes.byref(p), C1.ctypes.data, C2.ctypes.data,
+                                R.ctypes.data, qs[0].ctypes.data if qs[0] is not None else None,
+                                qs[1].ctypes.data if qs[1] is not None else None, device))
+        return cls(h_out, device)
+
+    @classmethod
+    def train(cls, learn, T, M, variant="global", iters=10, stream=None):
+        """Train codebooks on the GPU from an (n, D) float32 CUDA tensor of integer-valued vectors."""
+        import torch
+        assert learn.is_cuda and learn.dtype == torch.float32 and learn.is_contiguous()
+        v = VARIANT_LOCAL if variant == "local" else VARIANT_GLOBAL
+        p = cls._params(learn.shape[1], T, M, v, iters)
+        h_out = ctypes.c_void_p()
+        _check(lib().bpq_train_load(ctypes.byref(h_out), ctypes.byref(p), _ptr(learn), learn.shape[0], None,
+                                    learn.device.index or 0, _stream(stream)))
+        return cls(h_out, learn.device.index or 0)
+
+    @classmethod
+    def load(cls, path, device=0):
+        h_out = ctypes.c_void_p()
+        _check(lib().bpq_train_load(ctypes.byref(h_out), None, None, 0, str(path).encode(), device, None))
+        return cls(h_out, device)
+
+    def save(self, path):
+        _check(lib().bpq_save(self._h, str(path).encode()))
+
+    def close(self):
+        if self._h:
+            lib().bpq_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- building -------------------------------------------------------------
+    def encode(self, x, stream=None):
+        import torch
+        n = x.shape[0]
+        cells = torch.empty(n, dtype=torch.int32, device=x.device)
+        codes = torch.empty((n, self.params.M), dtype=torch.uint8, device=x.device)
+        _check(lib().bpq_encode(self._h, _ptr(x), n, _ptr(cells), _ptr(codes), _stream(stream)))
+        return cells, codes
+
+    def add(self, x, ids=None, stream=None):
+        _check(lib().bpq_add(self._h, _ptr(x), x.shape[0], _ptr(ids), _stream(stream)))
+
+    def finalize(self, stream=None):
+        _check(lib().bpq_finalize(self._h, _stream(stream)))
+
+    # -- introspection --------------------------------------------------------
+    def info(self):
+        out = Info()
+        _check(lib().bpq_get_info(self._h, ctypes.byref(out)))
+        return out
+
+    @property
+    def params(self):
+        return self.info().params
+
+    def arrays(self):
+        """Copies of the index arrays as CUDA tensors."""
+        import torch
+        a = Arrays()
+        _check(lib().bpq_get_arrays(self._h, ctypes.byref(a)))
+        inf = self.info()
+        p = inf.params
+        h, s, m2, n = p.D // 2, p.D // p.M, p.M // 2, inf.n_points
+        shapes = {"C1": ((p.T, h), "<f4"), "C2": ((p.T, h), "<f4"), "R": ((p.M, 256, s), "<f4"),
+                  "Q": ((p.T, m2, 256, s), "<f4"), "S": ((p.T, m2, 256, s), "<f4"),
+                  "X1": ((p.T, m2, 256), "<f4"), "X2": ((p.T, m2, 256), "<f4"),
+                  "offsets": ((p.T * p.T + 1,), "<u4"), "codes": ((n, p.M), "|u1"), "ids": ((n,), "<i4")}
+        out = {}
+        dev = torch.device("cuda", self.device)
+        for name, (shape, ts) in shapes.items():
+            ptr = getattr(a, name)
+            if not ptr or 0 in shape:
+                out[name] = None
+                continue
+            if ts == "<u4":  # torch has no uint32 copies everywhere: view as int32
+                ts = "<i4"
+            out[name] = torch.as_tensor(_CudaView(ptr, shape, ts), device=dev).clone()
+        return out
+
+    # -- queries --------------------------------------------------------------
+    def workspace(self, nq, L_max, k, scorer="fbpq", stream=None):
+        import torch
+        need = lib().bpq_search_workspace_size(self._h, nq, int(L_max), k, SCORERS[scorer])
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=torch.device("cuda", self.device))
+        return self._ws
+
+    def query_tables(self, q, lut=True, stream=None):
+        import torch
+        p = self.params
+        nq = q.shape[0]
+        d1 = torch.empty((nq, p.T), dtype=torch.float32, device=q.device)
+        d2 = torch.empty((nq, p.T), dtype=torch.float32, device=q.device)
+        lt = torch.empty((nq, p.M, 256), dtype=torch.float32, device=q.device) if lut else None
+        _check(lib().bpq_query_tables(self._h, _ptr(q), nq, _ptr(d1), _ptr(d2), _ptr(lt), _stream(stream)))
+        return d1, d2, lt
+
+    def traverse(self, q, L, cap, stream=None):
+        """Visited non-empty cells per query: (cells int32 (nq, cap, 4) raw bpq_cell, ncells, npoints)."""
+        import torch
+        nq = q.shape[0]
+        Ls, stride = _L_array(L, nq)
+        cells = torch.empty((nq, cap, 4), dtype=torch.int32, device=q.device)
+        ncells = torch.empty(nq, dtype=torch.int32, device=q.device)
+        npoints = torch.empty(nq, dtype=torch.int64, device=q.device)
+        ws = self.workspace(nq, int(Ls.max()), 1)
+        _check(lib().bpq_traverse(self._h, _ptr(q), nq, Ls.ctypes.data, stride, cap, _ptr(cells), _ptr(ncells),
+                                  _ptr(npoints), _ptr(ws), ws.numel(), _stream(stream)))
+        return cells, ncells, npoints
+
+    def search(self, q, L, k, scorer="fbpq", stream=None, workspace=None, out=None):
+        import torch
+        nq = q.shape[0]
+        Ls, stride = _L_array(L, nq)
+        if out is None:
+            ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+            dists = torch.empty((nq, k), dtype=torch.float32, device=q.device)
+        else:
+            ids, dists = out
+        ws = workspace if workspace is not None else self.workspace(nq, int(Ls.max()), k, scorer)
+        _check(lib().bpq_search(self._h, _ptr(q), nq, Ls.ctypes.data, stride, k, SCORERS[scorer], _ptr(ids),
+                                _ptr(dists), _ptr(ws), ws.numel(), _stream(stream)))
+        return ids, dists
+
+    def search_status(self, workspace=None, stream=None):
+        ws = workspace if workspace is not None else self._ws
+        _check(lib().bpq_search_status(self._h, _ptr(ws), _stream(stream)))
+
+    def search_host(self, q, L, k, scorer="fbpq", stream=None):
+        """Host numpy queries in, host numpy (ids, dists) out; copies are inside the call."""
+        q = np.ascontiguousarray(q, dtype=np.float32)
+        nq = q.shape[0]
+        Ls, stride = _L_array(L, nq)
+        ids = np.empty((nq, k), dtype=np.int32)
+        dists = np.empty((nq, k), dtype=np.float32)
+        _check(lib().bpq_search_host(self._h, q.ctypes.data, nq, Ls.ctypes.data, stride, k, SCORERS[scorer],
+                                     ids.ctypes.data, dists.ctypes.data, _stream(stream)))
+        return ids, dists
+
+
+def header_symbols():
+    """Function names declared in include/bpq.h."""
+    import re
+    hdr = open(os.path.join(os.path.dirname(HERE), "include", "bpq.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(bpq_\w+)\s*\(", hdr, flags=re.M)))

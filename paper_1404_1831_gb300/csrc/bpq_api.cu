@@ -1,0 +1,628 @@
+// C ABI entry points of libbpq (declared in include/bpq.h): index lifecycle,
+// workspace layout and the query pipeline
+//   tables (K1/K2) -> traversal (K4) -> scan + top-k (K5/K6)
+// enqueued on the caller's stream, chunk by chunk when the workspace is small.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bpq_internal.cuh"
+
+namespace bpq {
+bool ids_nonnegative(const int32_t* ids, int64_t n, cudaStream_t st);
+}
+
+using namespace bpq;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+template <typename F>
+int guard(F&& f) {
+  try {
+    g_last_error.clear();
+    f();
+    return BPQ_OK;
+  } catch (const Error& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return BPQ_ENOMEM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return BPQ_EINVAL;
+  }
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    BPQ_CUDA(cudaGetDevice(&prev));
+    if (prev != dev) BPQ_CUDA(cudaSetDevice(dev));
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != prev && prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+void check_params(const bpq_params* p) {
+  BPQ_CHECK(p, BPQ_EINVAL, "params is NULL");
+  BPQ_CHECK(p->ksub == KSUB, BPQ_EINVAL, "ksub must be 256");
+  BPQ_CHECK(p->D > 0 && p->D % 2 == 0, BPQ_EINVAL, "D must be positive and even");
+  BPQ_CHECK(p->M > 0 && p->M % 2 == 0 && (p->D / 2) % (p->M / 2) == 0, BPQ_EINVAL,
+            "M must be even with D/M dividing D/2");
+  BPQ_CHECK(p->T >= 1 && p->T <= MAX_T, BPQ_EINVAL, "T must be in [1, 4096]");
+  BPQ_CHECK(p->variant == BPQ_VARIANT_GLOBAL || p->variant == BPQ_VARIANT_LOCAL, BPQ_EINVAL, "bad variant");
+  BPQ_CHECK(p->kmeans_iters >= 0 && p->kmeans_iters <= 1000, BPQ_EINVAL, "kmeans_iters out of range");
+  BPQ_CHECK(scan_supported(p->D, p->M), BPQ_EINVAL,
+            "this build supports (D, M) in {(128, 8), (128, 16), (32, 8), (8, 8)}");
+}
+
+bpq_index* new_index(const bpq_params* p, int device) {
+  check_params(p);
+  int ndev = 0;
+  BPQ_CUDA(cudaGetDeviceCount(&ndev));
+  BPQ_CHECK(device >= 0 && device < ndev, BPQ_EINVAL, "bad device ordinal");
+  auto* ix = new bpq_index();
+  ix->p = *p;
+  ix->device = device;
+  ix->h = p->D / 2;
+  ix->s = p->D / p->M;
+  ix->m2 = p->M / 2;
+  BPQ_CUDA(cudaDeviceGetAttribute(&ix->sm_count, cudaDevAttrMultiProcessorCount, device));
+  return ix;
+}
+
+void empty_lists(bpq_index& ix, cudaStream_t st) {
+  const int64_t nc = (int64_t)ix.p.T * ix.p.T + 1;
+  ix.offsets.alloc(nc * 4);
+  BPQ_CUDA(cudaMemsetAsync(ix.offsets.p, 0, nc * 4, st));
+  ix.n_points = ix.n_nonempty = ix.max_cell = 0;
+}
+
+size_t cb_floats_R(const bpq_params& p) { return (size_t)p.M * KSUB * (p.D / p.M); }
+size_t cb_floats_local(const bpq_params& p) { return (size_t)p.T * (p.M / 2) * KSUB * (p.D / p.M); }
+
+// ---------------------------------------------------------------------------
+// Workspace layout for a chunk of nq queries.
+// ---------------------------------------------------------------------------
+struct Layout {
+  size_t status, qcounter, L, d1, d2, lut, cells, ncells, npoints, total;
+  int64_t cap;
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout layout(const bpq_index& ix, int64_t nq, int64_t L_max, int scorer, bool with_cells) {
+  Layout l{};
+  size_t o = 0;
+  l.status = o;
+  o = align_up(o + 4);
+  l.qcounter = o;
+  o = align_up(o + 4);
+  l.L = o;
+  o = align_up(o + (size_t)nq * 4);
+  l.d1 = o;
+  o = align_up(o + (size_t)nq * ix.p.T * 4);
+  l.d2 = o;
+  o = align_up(o + (size_t)nq * ix.p.T * 4);
+  l.lut = o;
+  if (scorer == BPQ_SCORER_FBPQ && with_cells) o = align_up(o + (size_t)nq * ix.p.M * KSUB * 4);
+  l.cap = std::max<int64_t>(1, std::min<int64_t>(L_max, std::max<int64_t>(ix.n_nonempty, 1)));
+  l.cells = o;
+  if (with_cells) o = align_up(o + (size_t)nq * l.cap * sizeof(bpq_cell));
+  l.ncells = o;
+  o = align_up(o + (size_t)nq * 4);
+  l.npoints = o;
+  o = align_up(o + (size_t)nq * 8);
+  l.total = o;
+  return l;
+}
+
+int64_t read_L(const int64_t* L_host, int64_t L_stride, int64_t nq, std::vector<int32_t>* per_query) {
+  BPQ_CHECK(L_host, BPQ_EINVAL, "L is NULL");
+  BPQ_CHECK(L_stride == 0 || L_stride == 1, BPQ_EINVAL, "L_stride must be 0 or 1");
+  int64_t L_max = 0;
+  const int64_t n = L_stride ? nq : 1;
+  if (per_query && L_stride) per_query->resize(nq);
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t v = L_host[i];
+    BPQ_CHECK(v >= 1 && v < ((int64_t)1 << 31), BPQ_EINVAL, "every L must be in [1, 2^31)");
+    L_max = std::max(L_max, v);
+    if (per_query && L_stride) (*per_query)[i] = (int32_t)v;
+  }
+  return L_max;
+}
+
+void check_searchable(const bpq_index* ix) {
+  BPQ_CHECK(ix, BPQ_EINVAL, "index is NULL");
+  BPQ_CHECK(ix->n_pending == 0, BPQ_ESTATE, "points were added since the last bpq_finalize");
+}
+
+// Runs tables + traversal (+ scan when ids/dists are given) over the queries in
+// chunks that fit the workspace.
+void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride,
+                 int k, int scorer, int32_t* out_ids, float* out_dists, bpq_cell* user_cells, int32_t user_cap,
+                 int32_t* user_ncells, int64_t* user_npoints, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const bool scan = user_cells == nullptr;
+  std::vector<int32_t> Lq;
+  const int64_t L_max = read_L(L_host, L_stride, nq, &Lq);
+  BPQ_CHECK(q || nq == 0, BPQ_EINVAL, "queries is NULL");
+  BPQ_CHECK(ws, BPQ_EINVAL, "workspace is NULL");
+  if (scan) {
+    BPQ_CHECK(k >= 1 && k <= MAX_K, BPQ_EINVAL, "k must be in [1, 1024]");
+    BPQ_CHECK(out_ids && out_dists, BPQ_EINVAL, "output pointers are NULL");
+    BPQ_CHECK(scorer >= BPQ_SCORER_FBPQ && scorer <= BPQ_SCORER_HBPQ, BPQ_EINVAL, "bad scorer");
+    if (scorer == BPQ_SCORER_HBPQ)
+      BPQ_CHECK(ix.p.variant == BPQ_VARIANT_LOCAL, BPQ_EINVAL, "the HBPQ scorer needs local codebooks");
+    else
+      BPQ_CHECK(ix.p.variant == BPQ_VARIANT_GLOBAL, BPQ_EINVAL,
+                "FBPQ and reconstruction scorers need global codebooks");
+  } else {
+    BPQ_CHECK(user_cap >= 1 && user_ncells && user_npoints, BPQ_EINVAL, "bad traversal outputs");
+  }
+  if (nq <= 0) return;
+  // largest chunk that fits
+  int64_t chunk = nq;
+  if (layout(ix, chunk, L_max, scorer, scan).total > ws_bytes) {
+    int64_t lo = 0, hi = nq;
+    while (hi - lo > 1) {
+      int64_t mid = (lo + hi) / 2;
+      if (layout(ix, mid, L_max, scorer, scan).total <= ws_bytes) lo = mid; else hi = mid;
+    }
+    chunk = lo;
+  }
+  BPQ_CHECK(chunk >= 1, BPQ_ECAPACITY, "workspace too small for one query");
+  const Layout l = layout(ix, chunk, L_max, scorer, scan);
+  char* w = static_cast<char*>(ws);
+  BPQ_CUDA(cudaMemsetAsync(w + l.status, 0, 4, st));
+  const float rho = (float)((double)ix.n_points / (double)std::max<int64_t>(1, ix.n_nonempty));
+  for (int64_t c0 = 0; c0 < nq; c0 += chunk) {
+    const int64_t nc = std::min(chunk, nq - c0);
+    const float* qc = q + c0 * ix.p.D;
+    float* d1 = reinterpret_cast<float*>(w + l.d1);
+    float* d2 = reinterpret_cast<float*>(w + l.d2);
+    float* lut = (scan && scorer == BPQ_SCORER_FBPQ) ? reinterpret_cast<float*>(w + l.lut) : nullptr;
+    launch_query_tables(ix, qc, nc, d1, d2, lut, st);
+    TraverseArgs ta{};
+    ta.d1 = d1;
+    ta.d2 = d2;
+    ta.offsets = ix.offsets.as<uint32_t>();
+    if (L_stride) {
+      BPQ_CUDA(cudaMemcpyAsync(w + l.L, Lq.data() + c0, nc * 4, cudaMemcpyHostToDevice, st));
+      ta.L = reinterpret_cast<const int32_t*>(w + l.L);
+    } else {
+      ta.L = nullptr;
+      ta.L_scalar = (int32_t)L_host[0];
+    }
+    ta.T = ix.p.T;
+    ta.rho = rho;
+    ta.status = reinterpret_cast<int32_t*>(w + l.status);
+    ta.nq = nc;
+    if (scan) {
+      ta.cap = (int32_t)l.cap;
+      ta.cells = reinterpret_cast<bpq_cell*>(w + l.cells);
+      ta.ncells = reinterpret_cast<int32_t*>(w + l.ncells);
+      ta.npoints = reinterpret_cast<int64_t*>(w + l.npoints);
+    } else {
+      ta.cap = user_cap;
+      ta.cells = user_cells + c0 * user_cap;
+      ta.ncells = user_ncells + c0;
+      ta.npoints = user_npoints + c0;
+    }
+    launch_traverse(ta, st);
+    if (!scan) continue;
+    ScanArgs sa{};
+    sa.cells = ta.cells;
+    sa.ncells = ta.ncells;
+    sa.cap = ta.cap;
+    sa.nq = nc;
+    sa.T = ix.p.T;
+    sa.M = ix.p.M;
+    sa.D = ix.p.D;
+    sa.k = k;
+    sa.lut = lut;
+    sa.X1 = ix.X1.as<float>();
+    sa.X2 = ix.X2.as<float>();
+    sa.queries = qc;
+    sa.C1 = ix.C1.as<float>();
+    sa.C2 = ix.C2.as<float>();
+    sa.R = ix.R.as<float>();
+    sa.Q = ix.Q.as<float>();
+    sa.S = ix.S.as<float>();
+    sa.codes = ix.codes.as<uint8_t>();
+    sa.ids = ix.ids.as<int32_t>();
+    sa.out_ids = out_ids + c0 * k;
+    sa.out_dists = out_dists + c0 * k;
+    sa.qcounter = reinterpret_cast<int32_t*>(w + l.qcounter);
+    sa.sm_count = ix.sm_count;
+    launch_scan(sa, scorer, st);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// File format: magic, version, params, n_points, then sections
+// (u64 size, bytes, u64 FNV-1a checksum).
+// ---------------------------------------------------------------------------
+const char MAGIC[8] = {'B', 'P', 'Q', 'I', 'D', 'X', 0, 1};
+
+uint64_t fnv1a(const void* data, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(data);
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+struct File {
+  FILE* f = nullptr;
+  ~File() {
+    if (f) fclose(f);
+  }
+};
+
+void write_section(FILE* f, const void* dev, size_t bytes) {
+  std::vector<unsigned char> host(bytes);
+  if (bytes) BPQ_CUDA(cudaMemcpy(host.data(), dev, bytes, cudaMemcpyDeviceToHost));
+  uint64_t n = bytes, h = fnv1a(host.data(), bytes);
+  BPQ_CHECK(fwrite(&n, 8, 1, f) == 1 && (bytes == 0 || fwrite(host.data(), 1, bytes, f) == bytes) &&
+                fwrite(&h, 8, 1, f) == 1,
+            BPQ_EIO, "write failed");
+}
+
+void read_section(FILE* f, DevBuf& dst, size_t bytes) {
+  uint64_t n = 0, h = 0;
+  BPQ_CHECK(fread(&n, 8, 1, f) == 1, BPQ_ECORRUPT, "truncated index file");
+  BPQ_CHECK(n == bytes, BPQ_ECORRUPT, "index file section has the wrong size");
+  std::vector<unsigned char> host(bytes);
+  BPQ_CHECK((bytes == 0 || fread(host.data(), 1, bytes, f) == bytes) && fread(&h, 8, 1, f) == 1, BPQ_ECORRUPT,
+            "truncated index file");
+  BPQ_CHECK(h == fnv1a(host.data(), bytes), BPQ_ECORRUPT, "index file checksum mismatch");
+  dst.alloc(bytes);
+  if (bytes) BPQ_CUDA(cudaMemcpy(dst.p, host.data(), bytes, cudaMemcpyHostToDevice));
+}
+
+bpq_index* load_file(const char* path, int device) {
+  File fh;
+  fh.f = fopen(path, "rb");
+  BPQ_CHECK(fh.f, BPQ_EIO, std::string("cannot open ") + path);
+  char magic[8];
+  uint32_t version = 0;
+  bpq_params p{};
+  int64_t n = 0;
+  BPQ_CHECK(fread(magic, 8, 1, fh.f) == 1 && memcmp(magic, MAGIC, 8) == 0, BPQ_ECORRUPT, "not a bpq index file");
+  BPQ_CHECK(fread(&version, 4, 1, fh.f) == 1 && version == 1, BPQ_ECORRUPT, "unsupported index file version");
+  BPQ_CHECK(fread(&p, sizeof(p), 1, fh.f) == 1 && fread(&n, 8, 1, fh.f) == 1, BPQ_ECORRUPT, "truncated header");
+  try {
+    check_params(&p);
+  } catch (const Error& e) {
+    throw Error(BPQ_ECORRUPT, std::string("bad params in index file: ") + e.what());
+  }
+  BPQ_CHECK(n >= 0 && n < ((int64_t)1 << 32) - 1, BPQ_ECORRUPT, "bad point count");
+  bpq_index* ix = new_index(&p, device);
+  try {
+    DeviceGuard dg(device);
+    const size_t hf = (size_t)p.T * (p.D / 2);
+    read_section(fh.f, ix->C1, hf * 4);
+    read_section(fh.f, ix->C2, hf * 4);
+    read_section(fh.f, ix->R, cb_floats_R(p) * 4);
+    if (p.variant == BPQ_VARIANT_LOCAL) {
+      read_section(fh.f, ix->Q, cb_floats_local(p) * 4);
+      read_section(fh.f, ix->S, cb_floats_local(p) * 4);
+    }
+    read_section(fh.f, ix->offsets, ((size_t)p.T * p.T + 1) * 4);
+    read_section(fh.f, ix->codes, (size_t)n * p.M);
+    read_section(fh.f, ix->ids, (size_t)n * 4);
+    // consistency of the offsets with the point count, and the cell statistics
+    std::vector<uint32_t> off((size_t)p.T * p.T + 1);
+    BPQ_CUDA(cudaMemcpy(off.data(), ix->offsets.p, off.size() * 4, cudaMemcpyDeviceToHost));
+    BPQ_CHECK(off[0] == 0 && off.back() == (uint64_t)n, BPQ_ECORRUPT, "offsets do not match the point count");
+    int64_t nonempty = 0, maxc = 0;
+    for (size_t c = 0; c + 1 < off.size(); ++c) {
+      BPQ_CHECK(off[c + 1] >= off[c], BPQ_ECORRUPT, "offsets are not monotone");
+      const int64_t cnt = off[c + 1] - off[c];
+      nonempty += cnt > 0;
+      maxc = std::max(maxc, cnt);
+    }
+    ix->n_points = n;
+    ix->n_nonempty = nonempty;
+    ix->max_cell = maxc;
+    build_fbpq_tables(*ix, 0);
+    BPQ_CUDA(cudaDeviceSynchronize());
+  } catch (...) {
+    delete ix;
+    throw;
+  }
+  return ix;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bpq_last_error(void) { return g_last_error.c_str(); }
+
+int bpq_create(bpq_index** out, const bpq_params* p, const float* C1_host, const float* C2_host,
+               const float* R_host, const float* Q_host, const float* S_host, int device) {
+  return guard([&] {
+    BPQ_CHECK(out, BPQ_EINVAL, "out is NULL");
+    *out = nullptr;
+    BPQ_CHECK(C1_host && C2_host && R_host, BPQ_EINVAL, "codebook pointer is NULL");
+    bpq_index* ix = new_index(p, device);
+    try {
+      DeviceGuard dg(device);
+      if (p->variant == BPQ_VARIANT_LOCAL) BPQ_CHECK(Q_host && S_host, BPQ_EINVAL, "local codebooks are NULL");
+      const size_t hf = (size_t)p->T * (p->D / 2);
+      ix->C1.alloc(hf * 4);
+      ix->C2.alloc(hf * 4);
+      ix->R.alloc(cb_floats_R(*p) * 4);
+      BPQ_CUDA(cudaMemcpy(ix->C1.p, C1_host, hf * 4, cudaMemcpyHostToDevice));
+      BPQ_CUDA(cudaMemcpy(ix->C2.p, C2_host, hf * 4, cudaMemcpyHostToDevice));
+      BPQ_CUDA(cudaMemcpy(ix->R.p, R_host, cb_floats_R(*p) * 4, cudaMemcpyHostToDevice));
+      if (p->variant == BPQ_VARIANT_LOCAL) {
+        ix->Q.alloc(cb_floats_local(*p) * 4);
+        ix->S.alloc(cb_floats_local(*p) * 4);
+        BPQ_CUDA(cudaMemcpy(ix->Q.p, Q_host, cb_floats_local(*p) * 4, cudaMemcpyHostToDevice));
+        BPQ_CUDA(cudaMemcpy(ix->S.p, S_host, cb_floats_local(*p) * 4, cudaMemcpyHostToDevice));
+      }
+      build_fbpq_tables(*ix, 0);
+      empty_lists(*ix, 0);
+      BPQ_CUDA(cudaDeviceSynchronize());
+    } catch (...) {
+      delete ix;
+      throw;
+    }
+    *out = ix;
+  });
+}
+
+int bpq_train_load(bpq_index** out, const bpq_params* p, const float* learn_dev, int64_t n_learn,
+                   const char* path, int device, void* stream) {
+  return guard([&] {
+    BPQ_CHECK(out, BPQ_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!learn_dev) {
+      BPQ_CHECK(path, BPQ_EINVAL, "neither learn vectors nor a path were given");
+      *out = load_file(path, device);
+      return;
+    }
+    bpq_index* ix = new_index(p, device);
+    try {
+      DeviceGuard dg(device);
+      cudaStream_t st = static_cast<cudaStream_t>(stream);
+      train_codebooks(*ix, learn_dev, n_learn, st);
+      build_fbpq_tables(*ix, st);
+      empty_lists(*ix, st);
+      BPQ_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+      delete ix;
+      throw;
+    }
+    *out = ix;
+  });
+}
+
+int bpq_encode(const bpq_index* ix, const float* x_dev, int64_t n, int32_t* cell_out_dev, uint8_t* codes_out_dev,
+               void* stream) {
+  return guard([&] {
+    BPQ_CHECK(ix, BPQ_EINVAL, "index is NULL");
+    BPQ_CHECK(n >= 0, BPQ_EINVAL, "n < 0");
+    if (n == 0) return;
+    BPQ_CHECK(x_dev && cell_out_dev && codes_out_dev, BPQ_EINVAL, "NULL pointer");
+    DeviceGuard dg(ix->device);
+    launch_encode(*ix, x_dev, n, cell_out_dev, codes_out_dev, static_cast<cudaStream_t>(stream));
+  });
+}
+
+int bpq_add(bpq_index* ix, const float* x_dev, int64_t n, const int32_t* ids_dev, void* stream) {
+  return guard([&] {
+    BPQ_CHECK(ix, BPQ_EINVAL, "index is NULL");
+    BPQ_CHECK(n >= 0, BPQ_EINVAL, "n < 0");
+    if (n == 0) return;
+    BPQ_CHECK(x_dev, BPQ_EINVAL, "x is NULL");
+    BPQ_CHECK(ix->n_points + ix->n_pending + n < ((int64_t)1 << 32) - 1, BPQ_EINVAL, "too many points");
+    DeviceGuard dg(ix->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (ids_dev) BPQ_CHECK(ids_nonnegative(ids_dev, n, st), BPQ_EINVAL, "ids must be >= 0");
+    const int M = ix->p.M;
+    const int64_t need = ix->n_pending + n;
+    if (need > ix->pend_cap) {
+      const int64_t cap = std::max<int64_t>(need, 2 * ix->pend_cap);
+      DevBuf c, k, d;
+      c.alloc(cap * 4);
+      k.alloc(cap * M);
+      d.alloc(cap * 4);
+      if (ix->n_pending) {
+        BPQ_CUDA(cudaMemcpyAsync(c.p, ix->pend_cells.p, ix->n_pending * 4, cudaMemcpyDeviceToDevice, st));
+        BPQ_CUDA(cudaMemcpyAsync(k.p, ix->pend_codes.p, ix->n_pending * M, cudaMemcpyDeviceToDevice, st));
+        BPQ_CUDA(cudaMemcpyAsync(d.p, ix->pend_ids.p, ix->n_pending * 4, cudaMemcpyDeviceToDevice, st));
+        BPQ_CUDA(cudaStreamSynchronize(st));
+      }
+      std::swap(c.p, ix->pend_cells.p);
+      std::swap(c.bytes, ix->pend_cells.bytes);
+      std::swap(k.p, ix->pend_codes.p);
+      std::swap(k.bytes, ix->pend_codes.bytes);
+      std::swap(d.p, ix->pend_ids.p);
+      std::swap(d.bytes, ix->pend_ids.bytes);
+      ix->pend_cap = cap;
+    }
+    launch_encode(*ix, x_dev, n, ix->pend_cells.as<int32_t>() + ix->n_pending,
+                  ix->pend_codes.as<uint8_t>() + ix->n_pending * M, st);
+    int32_t* idp = ix->pend_ids.as<int32_t>() + ix->n_pending;
+    if (ids_dev)
+      BPQ_CUDA(cudaMemcpyAsync(idp, ids_dev, n * 4, cudaMemcpyDeviceToDevice, st));
+    else
+      fill_sequential_ids(idp, n, ix->n_added, st);
+    ix->n_pending += n;
+    ix->n_added += n;
+  });
+}
+
+int bpq_finalize(bpq_index* ix, void* stream) {
+  return guard([&] {
+    BPQ_CHECK(ix, BPQ_EINVAL, "index is NULL");
+    DeviceGuard dg(ix->device);
+    finalize_lists(*ix, static_cast<cudaStream_t>(stream));
+  });
+}
+
+int bpq_query_tables(const bpq_index* ix, const float* q, int64_t nq, float* d1, float* d2, float* lut,
+                     void* stream) {
+  return guard([&] {
+    BPQ_CHECK(ix, BPQ_EINVAL, "index is NULL");
+    BPQ_CHECK(nq >= 0, BPQ_EINVAL, "nq < 0");
+    if (nq == 0) return;
+    BPQ_CHECK(q && d1 && d2, BPQ_EINVAL, "NULL pointer");
+    DeviceGuard dg(ix->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t step = 65535LL * 64;
+    for (int64_t c0 = 0; c0 < nq; c0 += step) {
+      const int64_t nc = std::min(step, nq - c0);
+      launch_query_tables(*ix, q + c0 * ix->p.D, nc, d1 + c0 * ix->p.T, d2 + c0 * ix->p.T,
+                          lut ? lut + c0 * ix->p.M * KSUB : nullptr, st);
+    }
+  });
+}
+
+size_t bpq_search_workspace_size(const bpq_index* ix, int64_t nq, int64_t L_max, int32_t k, int32_t scorer) {
+  (void)k;
+  if (!ix || nq < 0 || L_max < 1) return 0;
+  return layout(*ix, std::max<int64_t>(nq, 1), L_max, scorer, true).total;
+}
+
+int bpq_traverse(const bpq_index* ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride,
+                 int32_t cap, bpq_cell* cells, int32_t* ncells, int64_t* npoints, void* ws, size_t ws_bytes,
+                 void* stream) {
+  return guard([&] {
+    check_searchable(ix);
+    BPQ_CHECK(nq >= 0, BPQ_EINVAL, "nq < 0");
+    BPQ_CHECK(cells, BPQ_EINVAL, "cells is NULL");
+    DeviceGuard dg(ix->device);
+    run_queries(*ix, q, nq, L_host, L_stride, 1, BPQ_SCORER_FBPQ, nullptr, nullptr, cells, cap, ncells, npoints,
+                ws, ws_bytes, static_cast<cudaStream_t>(stream));
+  });
+}
+
+int bpq_search(const bpq_index* ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride,
+               int32_t k, int32_t scorer, int32_t* ids, float* dists, void* ws, size_t ws_bytes, void* stream) {
+  return guard([&] {
+    check_searchable(ix);
+    BPQ_CHECK(nq >= 0, BPQ_EINVAL, "nq < 0");
+    DeviceGuard dg(ix->device);
+    run_queries(*ix, q, nq, L_host, L_stride, k, scorer, ids, dists, nullptr, 0, nullptr, nullptr, ws, ws_bytes,
+                static_cast<cudaStream_t>(stream));
+  });
+}
+
+int bpq_search_status(const bpq_index* ix, void* ws, void* stream) {
+  return guard([&] {
+    BPQ_CHECK(ix && ws, BPQ_EINVAL, "NULL pointer");
+    DeviceGuard dg(ix->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t s = 0;
+    BPQ_CUDA(cudaMemcpyAsync(&s, ws, 4, cudaMemcpyDeviceToHost, st));  // status is the first word
+    BPQ_CUDA(cudaStreamSynchronize(st));
+    BPQ_CHECK(s == 0, BPQ_ECAPACITY, "a query overflowed a fixed-size buffer (band or cell list)");
+  });
+}
+
+int bpq_search_host(bpq_index* ix, const float* q_host, int64_t nq, const int64_t* L_host, int64_t L_stride,
+                    int32_t k, int32_t scorer, int32_t* ids_host, float* dists_host, void* stream) {
+  return guard([&] {
+    check_searchable(ix);
+    BPQ_CHECK(nq >= 0 && q_host && ids_host && dists_host, BPQ_EINVAL, "bad argument");
+    BPQ_CHECK(k >= 1 && k <= MAX_K, BPQ_EINVAL, "k must be in [1, 1024]");
+    if (nq == 0) return;
+    DeviceGuard dg(ix->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t L_max = read_L(L_host, L_stride, nq, nullptr);
+    const size_t want = std::min<size_t>(layout(*ix, nq, L_max, scorer, true).total, (size_t)4 << 30);
+    const size_t one = layout(*ix, 1, L_max, scorer, true).total;
+    ix->host_ws.ensure(std::max(want, one));
+    ix->host_q.ensure((size_t)nq * ix->p.D * 4);
+    ix->host_ids.ensure((size_t)nq * k * 4);
+    ix->host_dists.ensure((size_t)nq * k * 4);
+    BPQ_CUDA(cudaMemcpyAsync(ix->host_q.p, q_host, (size_t)nq * ix->p.D * 4, cudaMemcpyHostToDevice, st));
+    run_queries(*ix, ix->host_q.as<float>(), nq, L_host, L_stride, k, scorer, ix->host_ids.as<int32_t>(),
+                ix->host_dists.as<float>(), nullptr, 0, nullptr, nullptr, ix->host_ws.p, ix->host_ws.bytes, st);
+    BPQ_CUDA(cudaMemcpyAsync(ids_host, ix->host_ids.p, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));
+    BPQ_CUDA(cudaMemcpyAsync(dists_host, ix->host_dists.p, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));
+    BPQ_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+int bpq_get_info(const bpq_index* ix, bpq_info* out) {
+  return guard([&] {
+    BPQ_CHECK(ix && out, BPQ_EINVAL, "NULL pointer");
+    out->n_points = ix->n_points;
+    out->n_pending = ix->n_pending;
+    out->n_nonempty = ix->n_nonempty;
+    out->max_cell = ix->max_cell;
+    out->device_bytes = (int64_t)(ix->C1.bytes + ix->C2.bytes + ix->R.bytes + ix->Q.bytes + ix->S.bytes +
+                                  ix->X1.bytes + ix->X2.bytes + ix->offsets.bytes + ix->codes.bytes +
+                                  ix->ids.bytes + ix->pend_cells.bytes + ix->pend_codes.bytes +
+                                  ix->pend_ids.bytes);
+    out->params = ix->p;
+  });
+}
+
+int bpq_get_arrays(const bpq_index* ix, bpq_arrays* out) {
+  return guard([&] {
+    BPQ_CHECK(ix && out, BPQ_EINVAL, "NULL pointer");
+    out->C1 = ix->C1.as<float>();
+    out->C2 = ix->C2.as<float>();
+    out->R = ix->R.as<float>();
+    out->Q = ix->Q.as<float>();
+    out->S = ix->S.as<float>();
+    out->X1 = ix->X1.as<float>();
+    out->X2 = ix->X2.as<float>();
+    out->offsets = ix->offsets.as<uint32_t>();
+    out->codes = ix->codes.as<uint8_t>();
+    out->ids = ix->ids.as<int32_t>();
+  });
+}
+
+int bpq_save(const bpq_index* ix, const char* path) {
+  return guard([&] {
+    check_searchable(ix);
+    BPQ_CHECK(path, BPQ_EINVAL, "path is NULL");
+    DeviceGuard dg(ix->device);
+    BPQ_CUDA(cudaDeviceSynchronize());
+    File fh;
+    fh.f = fopen(path, "wb");
+    BPQ_CHECK(fh.f, BPQ_EIO, std::string("cannot open ") + path + " for writing");
+    const uint32_t version = 1;
+    const int64_t n = ix->n_points;
+    BPQ_CHECK(fwrite(MAGIC, 8, 1, fh.f) == 1 && fwrite(&version, 4, 1, fh.f) == 1 &&
+                  fwrite(&ix->p, sizeof(ix->p), 1, fh.f) == 1 && fwrite(&n, 8, 1, fh.f) == 1,
+              BPQ_EIO, "write failed");
+    write_section(fh.f, ix->C1.p, ix->C1.bytes);
+    write_section(fh.f, ix->C2.p, ix->C2.bytes);
+    write_section(fh.f, ix->R.p, ix->R.bytes);
+    if (ix->p.variant == BPQ_VARIANT_LOCAL) {
+      write_section(fh.f, ix->Q.p, ix->Q.bytes);
+      write_section(fh.f, ix->S.p, ix->S.bytes);
+    }
+    write_section(fh.f, ix->offsets.p, ((size_t)ix->p.T * ix->p.T + 1) * 4);
+    write_section(fh.f, ix->codes.p, (size_t)n * ix->p.M);
+    write_section(fh.f, ix->ids.p, (size_t)n * 4);
+    BPQ_CHECK(fflush(fh.f) == 0, BPQ_EIO, "write failed");
+  });
+}
+
+void bpq_free(bpq_index* ix) {
+  if (!ix) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ix->device);
+  delete ix;
+  if (prev >= 0) cudaSetDevice(prev);
+}
+
+}  // extern "C"

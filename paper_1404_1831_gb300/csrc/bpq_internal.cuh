@@ -1,0 +1,230 @@
+// Internal declarations shared by the translation units of libbpq.
+// Device helpers, launch wrappers and the index object.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+
+#include "../../include/bpq.h"
+
+namespace bpq {
+
+constexpr int KSUB = 256;
+constexpr int MAX_T = 4096;
+constexpr int MAX_K = 1024;
+
+// ---------------------------------------------------------------------------
+// Errors: host code throws Error; the C ABI layer turns it into a return code.
+// ---------------------------------------------------------------------------
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define BPQ_CUDA(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      throw ::bpq::Error(e_ == cudaErrorMemoryAllocation ? BPQ_ENOMEM : BPQ_ECUDA,           \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                \
+  } while (0)
+
+#define BPQ_CHECK(cond, code, msg)                                                           \
+  do {                                                                                       \
+    if (!(cond)) throw ::bpq::Error((code), (msg));                                          \
+  } while (0)
+
+inline void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Error(BPQ_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// Order-preserving map between float and uint32 (for sort keys): a < b as floats
+// iff ord(a) < ord(b) as unsigned, for all non-NaN values.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t f2ord(float f) {
+  uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t o) {
+  uint32_t b = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+  return __uint_as_float(b);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Block-wide bitonic sort (ascending) of n = power of two 64-bit keys in shared
+// memory; all threads of the block must call it.
+__device__ __forceinline__ void block_bitonic_sort(uint64_t* a, int n) {
+  for (int size = 2; size <= n; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) {
+        int lo = 2 * t - (t & (stride - 1));
+        int hi = lo + stride;
+        bool up = ((lo & size) == 0);
+        uint64_t x = a[lo], y = a[hi];
+        if ((x > y) == up) {
+          a[lo] = y;
+          a[hi] = x;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Warp-wide bitonic sort (ascending) of n = power of two keys in shared memory
+// (n >= 64); only the calling warp touches `a`.
+__device__ __forceinline__ void warp_bitonic_sort(uint64_t* a, int n) {
+  const int lane = threadIdx.x & 31;
+  for (int size = 2; size <= n; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncwarp();
+      for (int t = lane; t < (n >> 1); t += 32) {
+        int lo = 2 * t - (t & (stride - 1));
+        int hi = lo + stride;
+        bool up = ((lo & size) == 0);
+        uint64_t x = a[lo], y = a[hi];
+        if ((x > y) == up) {
+          a[lo] = y;
+          a[hi] = x;
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Index object (host side).
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void alloc(size_t b) {
+    release();
+    if (b == 0) return;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      throw Error(BPQ_ENOMEM, std::string("cudaMalloc(") + std::to_string(b) + "): " + cudaGetErrorString(e));
+    }
+    bytes = b;
+  }
+  void ensure(size_t b) {
+    if (b > bytes) alloc(b);
+  }
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+}  // namespace bpq
+
+struct bpq_index {
+  bpq_params p{};
+  int device = 0;
+  int sm_count = 0;
+  int h = 0, s = 0, m2 = 0;  // D/2, D/M, M/2
+  bpq::DevBuf C1, C2, R, Q, S, X1, X2;
+  // pending points (encoded, not yet in the lists)
+  bpq::DevBuf pend_cells, pend_codes, pend_ids;
+  int64_t n_pending = 0, pend_cap = 0;
+  int64_t n_added = 0;  // for default ids
+  // finalized lists
+  bpq::DevBuf offsets, codes, ids;
+  int64_t n_points = 0, n_nonempty = 0, max_cell = 0;
+  // workspace owned by bpq_search_host
+  bpq::DevBuf host_ws, host_q, host_ids, host_dists;
+};
+
+namespace bpq {
+
+// ---------------------------------------------------------------------------
+// Launch wrappers (defined in the .cu files).
+// ---------------------------------------------------------------------------
+
+// Query tables (bpq_tables.cu).
+void launch_query_tables(const bpq_index& ix, const float* q, int64_t nq, float* d1, float* d2,
+                         float* lut, cudaStream_t st);
+void build_fbpq_tables(bpq_index& ix, cudaStream_t st);
+
+// Traversal (bpq_traverse.cu).
+struct TraverseArgs {
+  const float* d1;
+  const float* d2;
+  const uint32_t* offsets;
+  const int32_t* L;  // per query, or nullptr -> L_scalar
+  int32_t L_scalar;
+  int32_t T;
+  int32_t cap;       // output cells per query
+  float rho;         // mean points per non-empty cell (sizes the first band)
+  bpq_cell* cells;   // nq x cap
+  int32_t* ncells;
+  int64_t* npoints;
+  int32_t* status;   // single word, set to 1 on overflow
+  int64_t nq;
+};
+void launch_traverse(const TraverseArgs& a, cudaStream_t st);
+int traverse_band_capacity();
+
+// Scans (bpq_scan.cu).
+struct ScanArgs {
+  const bpq_cell* cells;
+  const int32_t* ncells;
+  int32_t cap;
+  int64_t nq;
+  int32_t T, M, D, k;
+  const float* lut;      // nq x M x 256 (FBPQ)
+  const float* X1;       // T x M/2 x 256
+  const float* X2;
+  const float* queries;  // nq x D (recon / hbpq)
+  const float* C1;
+  const float* C2;
+  const float* R;        // M x 256 x D/M
+  const float* Q;        // T x M/2 x 256 x D/M (hbpq)
+  const float* S;
+  const uint8_t* codes;
+  const int32_t* ids;
+  int32_t* out_ids;
+  float* out_dists;
+  int32_t* qcounter;     // work counter for persistent kernels (zeroed by the launcher)
+  int sm_count;
+};
+void launch_scan(const ScanArgs& a, int scorer, cudaStream_t st);
+bool scan_supported(int D, int M);  // (D, M) shapes the scan kernels are built for
+
+// Index build (bpq_build.cu).
+void launch_encode(const bpq_index& ix, const float* x, int64_t n, int32_t* cell, uint8_t* codes,
+                   cudaStream_t st);
+void finalize_lists(bpq_index& ix, cudaStream_t st);
+void train_codebooks(bpq_index& ix, const float* learn, int64_t n, cudaStream_t st);
+void fill_sequential_ids(int32_t* ids, int64_t n, int64_t start, cudaStream_t st);
+
+}  // namespace bpq

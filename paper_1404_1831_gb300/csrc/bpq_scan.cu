@@ -1,0 +1,440 @@
+// Candidate scans and top-k selection (§2.3.3 reranking, §3.1 FBPQ, §3.2 HBPQ).
+//
+// Input: the visited non-empty cells of each query (bpq_cell lists written by the
+// traversal).  Every point of those cells is a candidate; the scan computes its
+// approximate squared distance and keeps the k smallest (distance, id) pairs.
+//
+//  * FBPQ (§3.1): with the per-query tables in shared memory, a candidate with
+//    code [r_1..r_M] in cell (i, j) costs M table lookups plus M lookups into the
+//    query-independent cross tables (Eq. 9):
+//       key(i,j) + sum_k ( lut[k][r_k] + X[k][r_k] ),  X = X1[i] for k < M/2, X2[j] else
+//    where key(i, j) = d1[i] + d2[j] = ||q - [c^1_i; c^2_j]||^2.
+//  * Reconstruction (Multi-D-ADC, §2.3.3): per visited cell the query displacement
+//    q - [c^1_i; c^2_j] is staged in shared memory, and every candidate costs an
+//    O(D) distance to its reconstructed displacement [R_1[r_1] .. R_M[r_M]].
+//  * HBPQ (§3.2): the same O(D) reconstruction with the local codebooks Q^i_k and
+//    S^j_k of the cell's two half-cells.
+//
+// Top-k: each warp keeps a sorted list of its best KP >= k composites
+// (ord(distance) << 32 | id) in shared memory plus a buffer of new candidates;
+// a full buffer is merged by a warp-wide bitonic sort.  A block-wide threshold
+// (the smallest k-th best of any warp) filters candidates; ids are read only for
+// candidates that pass it.  At the end the warp lists are merged by rank.
+#include <algorithm>
+
+#include "bpq_internal.cuh"
+
+namespace bpq {
+namespace {
+
+constexpr uint64_t EMPTY = ~0ull;
+
+template <int KP>
+struct WarpTopK {
+  static constexpr int AREA = 2 * (KP > 64 ? KP : 64);
+  static constexpr int BUF = AREA - KP;
+  uint64_t* area;
+  int nbuf;
+  __device__ void init(uint64_t* a) {
+    area = a;
+    nbuf = 0;
+    for (int i = threadIdx.x & 31; i < AREA; i += 32) area[i] = EMPTY;
+    __syncwarp();
+  }
+  __device__ void flush(int k, unsigned long long* thr) {
+    warp_bitonic_sort(area, AREA);
+    for (int i = KP + (threadIdx.x & 31); i < AREA; i += 32) area[i] = EMPTY;
+    nbuf = 0;
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) atomicMin(thr, (unsigned long long)area[k - 1]);
+    __syncwarp();
+  }
+  // Warp-collective: every lane calls with its own (accept, composite).
+  __device__ void offer(bool acc, uint64_t comp, int k, unsigned long long* thr) {
+    const unsigned m = __ballot_sync(0xffffffffu, acc);
+    if (!m) return;
+    if (acc) area[KP + nbuf + __popc(m & lanemask_lt())] = comp;
+    nbuf += __popc(m);
+    if (nbuf > BUF - 32) {
+      __syncwarp();
+      flush(k, thr);
+    }
+  }
+};
+
+// Merge NW sorted warp lists (stride AREA, first KP entries) into the k best,
+// written to out_ids / out_dists.  Ties between equal composites are broken by
+// warp index, so every element gets a distinct rank.
+__device__ void merge_lists(const uint64_t* areas, int NW, int KP, int AREA, int k, int32_t* out_ids,
+                            float* out_dists) {
+  const int total = NW * KP;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int w = e / KP, r = e % KP;
+    const uint64_t x = areas[w * AREA + r];
+    int rank = r;
+    for (int w2 = 0; w2 < NW && rank < k; ++w2) {
+      if (w2 == w) continue;
+      const uint64_t* b = areas + w2 * AREA;
+      int lo = 0, hi = KP;
+      if (w2 < w) {
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (b[mid] <= x) lo = mid + 1; else hi = mid;
+        }
+      } else {
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (b[mid] < x) lo = mid + 1; else hi = mid;
+        }
+      }
+      rank += lo;
+    }
+    if (rank < k) {
+      out_ids[rank] = (x == EMPTY) ? -1 : (int32_t)(uint32_t)x;
+      out_dists[rank] = (x == EMPTY) ? __int_as_float(0x7f800000) : ord2f((uint32_t)(x >> 32));
+    }
+  }
+}
+
+// Code words of one point: M bytes as M/4 32-bit words.
+template <int M>
+struct Code {
+  uint32_t w[M / 4];
+  __device__ __forceinline__ void load(const uint8_t* codes, uint32_t pos) {
+    if constexpr (M == 4) {
+      w[0] = __ldg(reinterpret_cast<const uint32_t*>(codes) + pos);
+    } else if constexpr (M == 8) {
+      uint2 v = __ldg(reinterpret_cast<const uint2*>(codes) + pos);
+      w[0] = v.x;
+      w[1] = v.y;
+    } else {
+      static_assert(M == 16, "M must be 4, 8 or 16");
+      uint4 v = __ldg(reinterpret_cast<const uint4*>(codes) + pos);
+      w[0] = v.x;
+      w[1] = v.y;
+      w[2] = v.z;
+      w[3] = v.w;
+    }
+  }
+  __device__ __forceinline__ uint32_t byte(int k) const { return (w[k >> 2] >> (8 * (k & 3))) & 0xffu; }
+};
+
+// Last index c in [0, n) with pref[c] <= f (pref strictly increasing, pref[0] = 0).
+__device__ __forceinline__ int find_cell(const int* pref, int n, int f) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (pref[mid] <= f) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Exclusive scan of one int per thread over the block (NT threads); returns the
+// exclusive prefix and writes the total to *total.  Uses tmp[NT/32 + 1].
+template <int NT>
+__device__ int block_excl_scan(int x, int* tmp, int* total) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  int v = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, v, o);
+    if (l >= o) v += y;
+  }
+  __syncthreads();
+  if (l == 31) tmp[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int t = (l < NT / 32) ? tmp[l] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (l >= o) t += y;
+    }
+    if (l < NT / 32) tmp[l] = t;
+  }
+  __syncthreads();
+  *total = tmp[NT / 32 - 1];
+  return v - x + (w > 0 ? tmp[w - 1] : 0);
+}
+
+// ---------------------------------------------------------------------------
+// FBPQ scan: one CTA per query.
+// ---------------------------------------------------------------------------
+template <int M, int KP>
+__global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
+  constexpr int NT = 256, NW = NT / 32, CH = NT, ILP = 4, M2 = M / 2;
+  using TK = WarpTopK<KP>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* lut = reinterpret_cast<float*>(smem);
+  uint64_t* areas = reinterpret_cast<uint64_t*>(lut + M * KSUB);
+  __shared__ uint32_t c_beg[CH];
+  __shared__ uint32_t c_x1[CH];
+  __shared__ uint32_t c_x2[CH];
+  __shared__ float c_key[CH];
+  __shared__ int c_pref[CH + 1];
+  __shared__ int scan_tmp[NW + 1];
+  __shared__ unsigned long long thr;
+  const int warp = threadIdx.x >> 5;
+  const int k = a.k;
+
+  for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < M * KSUB; t += NT) lut[t] = a.lut[q * M * KSUB + t];
+    TK tk;
+    tk.init(areas + warp * TK::AREA);
+    if (threadIdx.x == 0) thr = EMPTY;
+    const int nc = max(0, a.ncells[q]);
+    const bpq_cell* cl = a.cells + q * (int64_t)a.cap;
+    for (int cs = 0; cs < nc; cs += CH) {
+      const int nch = min(CH, nc - cs);
+      int cnt = 0;
+      if ((int)threadIdx.x < nch) {
+        bpq_cell c = cl[cs + threadIdx.x];
+        uint32_t i = c.cell / (uint32_t)a.T, j = c.cell % (uint32_t)a.T;
+        c_beg[threadIdx.x] = c.begin;
+        c_key[threadIdx.x] = c.key;
+        c_x1[threadIdx.x] = i * M2 * KSUB;
+        c_x2[threadIdx.x] = j * M2 * KSUB;
+        cnt = (int)c.count;
+      }
+      int total;
+      int ex = block_excl_scan<NT>(cnt, scan_tmp, &total);
+      if ((int)threadIdx.x < nch) c_pref[threadIdx.x] = ex;
+      __syncthreads();
+      const int P = total;
+      for (int base = 0; base < P; base += NT * ILP) {
+        Code<M> code[ILP];
+        int cidx[ILP];
+        uint32_t pos[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+          const int f = base + u * NT + threadIdx.x;
+          cidx[u] = -1;
+          if (f < P) {
+            const int c = find_cell(c_pref, nch, f);
+            cidx[u] = c;
+            pos[u] = c_beg[c] + (uint32_t)(f - c_pref[c]);
+            code[u].load(a.codes, pos[u]);
+          }
+        }
+        const unsigned long long th = *(volatile unsigned long long*)&thr;
+        const uint32_t th_hi = (uint32_t)(th >> 32);
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+          bool acc = false;
+          uint64_t comp = 0;
+          if (cidx[u] >= 0) {
+            const int c = cidx[u];
+            const float* x1 = a.X1 + c_x1[c];
+            const float* x2 = a.X2 + c_x2[c];
+            float part = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < M; ++kk) {
+              const uint32_t b = code[u].byte(kk);
+              const float xv = (kk < M2) ? __ldg(x1 + kk * KSUB + b) : __ldg(x2 + (kk - M2) * KSUB + b);
+              part += lut[kk * KSUB + b] + xv;
+            }
+            const float dist = c_key[c] + part;
+            const uint32_t o = f2ord(dist);
+            if (o <= th_hi) {
+              comp = ((uint64_t)o << 32) | (uint32_t)__ldg(a.ids + pos[u]);
+              acc = comp < th;
+            }
+          }
+          tk.offer(acc, comp, k, &thr);
+        }
+      }
+      __syncthreads();
+    }
+    if (tk.nbuf > 0) tk.flush(k, &thr);
+    __syncthreads();
+    merge_lists(areas, NW, KP, TK::AREA, k, a.out_ids + q * k, a.out_dists + q * k);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reconstruction scans (Multi-D-ADC and HBPQ): persistent CTAs, one query at a
+// time per CTA.
+// ---------------------------------------------------------------------------
+template <int M, int SUB, int KP, int NW, bool LOCAL>
+__global__ void __launch_bounds__(NW * 32) recon_scan_kernel(ScanArgs a) {
+  constexpr int NT = NW * 32, D = M * SUB, H = D / 2, M2 = M / 2, CHR = 32, ILP = 2;
+  constexpr int RS = SUB + 1;  // padded codeword stride
+  constexpr int QS = D + 1;    // padded displacement stride
+  using TK = WarpTopK<KP>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* areas = reinterpret_cast<uint64_t*>(smem);
+  float* rq = reinterpret_cast<float*>(areas + NW * TK::AREA);  // CHR x QS
+  float* Rs = rq + CHR * QS;                                     // M x 256 x RS (global codebooks)
+  __shared__ uint32_t c_beg[CHR];
+  __shared__ uint32_t c_i[CHR];
+  __shared__ uint32_t c_j[CHR];
+  __shared__ int c_pref[CHR + 1];
+  __shared__ int scan_tmp[NW + 1];
+  __shared__ unsigned long long thr;
+  __shared__ int64_t q_s;
+  const int warp = threadIdx.x >> 5;
+  const int k = a.k;
+  if (!LOCAL) {
+    for (int t = threadIdx.x; t < M * KSUB * SUB; t += NT) {
+      const int row = t / SUB, d = t % SUB;
+      Rs[row * RS + d] = a.R[t];
+    }
+  }
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) q_s = atomicAdd(a.qcounter, 1);
+    __syncthreads();
+    const int64_t q = q_s;
+    if (q >= a.nq) break;
+    const float* qv = a.queries + q * D;
+    TK tk;
+    tk.init(areas + warp * TK::AREA);
+    if (threadIdx.x == 0) thr = EMPTY;
+    const int nc = max(0, a.ncells[q]);
+    const bpq_cell* cl = a.cells + q * (int64_t)a.cap;
+    for (int cs = 0; cs < nc; cs += CHR) {
+      const int nch = min(CHR, nc - cs);
+      int cnt = 0;
+      if ((int)threadIdx.x < nch) {
+        bpq_cell c = cl[cs + threadIdx.x];
+        c_beg[threadIdx.x] = c.begin;
+        c_i[threadIdx.x] = c.cell / (uint32_t)a.T;
+        c_j[threadIdx.x] = c.cell % (uint32_t)a.T;
+        cnt = (int)c.count;
+      }
+      int total;
+      int ex = block_excl_scan<NT>(cnt, scan_tmp, &total);
+      if ((int)threadIdx.x < nch) c_pref[threadIdx.x] = ex;
+      __syncthreads();
+      // query displacement from each cell centroid: q - [c^1_i; c^2_j]
+      for (int t = threadIdx.x; t < nch * D; t += NT) {
+        const int c = t / D, d = t % D;
+        const float cen = (d < H) ? a.C1[(int64_t)c_i[c] * H + d] : a.C2[(int64_t)c_j[c] * H + d - H];
+        rq[c * QS + d] = qv[d] - cen;
+      }
+      __syncthreads();
+      const int P = total;
+      for (int base = 0; base < P; base += NT * ILP) {
+        Code<M> code[ILP];
+        int cidx[ILP];
+        uint32_t pos[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+          const int f = base + u * NT + threadIdx.x;
+          cidx[u] = -1;
+          if (f < P) {
+            const int c = find_cell(c_pref, nch, f);
+            cidx[u] = c;
+            pos[u] = c_beg[c] + (uint32_t)(f - c_pref[c]);
+            code[u].load(a.codes, pos[u]);
+          }
+        }
+        const unsigned long long th = *(volatile unsigned long long*)&thr;
+        const uint32_t th_hi = (uint32_t)(th >> 32);
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+          bool acc = false;
+          uint64_t comp = 0;
+          if (cidx[u] >= 0) {
+            const int c = cidx[u];
+            const float* r = rq + c * QS;
+            float dist = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < M; ++kk) {
+              const uint32_t b = code[u].byte(kk);
+              if (LOCAL) {
+                const float* w = (kk < M2)
+                    ? a.Q + (((int64_t)c_i[c] * M2 + kk) * KSUB + b) * SUB
+                    : a.S + (((int64_t)c_j[c] * M2 + kk - M2) * KSUB + b) * SUB;
+#pragma unroll
+                for (int d = 0; d < SUB; ++d) {
+                  const float t = r[kk * SUB + d] - __ldg(w + d);
+                  dist = fmaf(t, t, dist);
+                }
+              } else {
+                const float* w = Rs + (kk * KSUB + b) * RS;
+#pragma unroll
+                for (int d = 0; d < SUB; ++d) {
+                  const float t = r[kk * SUB + d] - w[d];
+                  dist = fmaf(t, t, dist);
+                }
+              }
+            }
+            const uint32_t o = f2ord(dist);
+            if (o <= th_hi) {
+              comp = ((uint64_t)o << 32) | (uint32_t)__ldg(a.ids + pos[u]);
+              acc = comp < th;
+            }
+          }
+          tk.offer(acc, comp, k, &thr);
+        }
+      }
+      __syncthreads();
+    }
+    if (tk.nbuf > 0) tk.flush(k, &thr);
+    __syncthreads();
+    merge_lists(areas, NW, KP, TK::AREA, k, a.out_ids + q * k, a.out_dists + q * k);
+  }
+}
+
+template <int M, int KP>
+void run_fbpq(const ScanArgs& a, cudaStream_t st) {
+  using TK = WarpTopK<KP>;
+  const size_t smem = (size_t)M * KSUB * 4 + (size_t)8 * TK::AREA * 8;
+  BPQ_CUDA(cudaFuncSetAttribute(fbpq_scan_kernel<M, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
+  fbpq_scan_kernel<M, KP><<<grid, 256, smem, st>>>(a);
+  check_launch("fbpq scan kernel");
+}
+
+template <int M, int SUB, int KP, bool LOCAL>
+void run_recon(const ScanArgs& a, cudaStream_t st) {
+  constexpr int NW = KP <= 128 ? 16 : (KP <= 256 ? 8 : (KP <= 512 ? 4 : 2));
+  using TK = WarpTopK<KP>;
+  const size_t smem = (size_t)NW * TK::AREA * 8 + (size_t)32 * (M * SUB + 1) * 4 +
+                      (LOCAL ? 0 : (size_t)M * KSUB * (SUB + 1) * 4);
+  BPQ_CHECK(smem <= 227 * 1024, BPQ_EINVAL, "reconstruction scan: codebooks do not fit shared memory");
+  auto kern = recon_scan_kernel<M, SUB, KP, NW, LOCAL>;
+  BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BPQ_CUDA(cudaMemsetAsync(a.qcounter, 0, sizeof(int32_t), st));
+  const int grid = (int)std::min<int64_t>(a.nq, (int64_t)a.sm_count);
+  kern<<<grid, NW * 32, smem, st>>>(a);
+  check_launch("reconstruction scan kernel");
+}
+
+template <int M, int SUB, int KP>
+void dispatch_scorer(const ScanArgs& a, int scorer, cudaStream_t st) {
+  if (scorer == BPQ_SCORER_FBPQ)
+    run_fbpq<M, KP>(a, st);
+  else if (scorer == BPQ_SCORER_RECON)
+    run_recon<M, SUB, KP, false>(a, st);
+  else
+    run_recon<M, SUB, KP, true>(a, st);
+}
+
+template <int M, int SUB>
+void dispatch_k(const ScanArgs& a, int scorer, cudaStream_t st) {
+  if (a.k <= 32) dispatch_scorer<M, SUB, 32>(a, scorer, st);
+  else if (a.k <= 128) dispatch_scorer<M, SUB, 128>(a, scorer, st);
+  else dispatch_scorer<M, SUB, 1024>(a, scorer, st);
+}
+
+}  // namespace
+
+bool scan_supported(int D, int M) {
+  return (D == 128 && (M == 8 || M == 16)) || (D == 32 && M == 8) || (D == 8 && M == 8);
+}
+
+void launch_scan(const ScanArgs& a, int scorer, cudaStream_t st) {
+  if (a.nq <= 0) return;
+  BPQ_CHECK(a.k >= 1 && a.k <= MAX_K, BPQ_EINVAL, "k must be in [1, 1024]");
+  const int D = a.D, M = a.M;
+  if (D == 128 && M == 8) dispatch_k<8, 16>(a, scorer, st);
+  else if (D == 128 && M == 16) dispatch_k<16, 8>(a, scorer, st);
+  else if (D == 32 && M == 8) dispatch_k<8, 4>(a, scorer, st);
+  else if (D == 8 && M == 8) dispatch_k<8, 1>(a, scorer, st);
+  else throw Error(BPQ_EINVAL, "unsupported (D, M) for the scan kernels");
+}
+
+}  // namespace bpq
