@@ -1,0 +1,507 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the bilayer product-quantization search path on GB300.
+
+Workload (synthetic, SIFT-shaped, generated on the device from synthdata):
+10,000,000 points of dimension 128 (integer coordinates in [0, 255]), an inverted
+multi-index with T = 1024 coarse codewords per half (1,048,576 cells), M = 8
+residual PQ codes of 256 codewords, codebooks trained on the GPU with 10 Lloyd
+iterations on 1,024,000 learn points; 10,000 queries per step at candidate
+budget L = 10,000, top-100 returned, FBPQ scoring.
+
+One step = bpq_search over the 10,000 queries (query tables, traversal, scan,
+top-k) with queries, index and workspace resident in HBM.  L2 (129 MB) is flushed
+between steps by writing a 512 MB buffer outside the timed events.
+
+  python bench.py [--gpus N --steps K --warmup W]      our CUDA path (torchrun for N > 1)
+  python bench.py --impl reference ...                 the FP64 CPU oracle on the host cores
+
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "queries/s at fixed L & Recall@10, FBPQ vs reconstruct-ADC; p50/p99 serve latency"
+UNIT = "queries/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--L", type=int, default=10_000)
+    ap.add_argument("--k", type=int, default=100)
+    ap.add_argument("--scorer", default="fbpq")
+    ap.add_argument("--n-base", type=int, default=None, help="override the point count (testing only)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the L / scorer sweep")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(args):
+    import dataclasses
+
+    import synthdata as sd
+    w = sd.SIFT10M
+    if args.n_base:
+        w = dataclasses.replace(w, n_base=args.n_base)
+    return w
+
+
+# ---------------------------------------------------------------------------
+# Oracle (CPU) side: runs in spawned processes only.
+# ---------------------------------------------------------------------------
+ORACLE_LEARN = 100_000
+ORACLE_ITERS = 4
+
+
+def _oracle_encode_chunk(task):
+    import synthdata as sd
+    from oracle import bpq_oracle as O
+    seed, n_comp, start, count, cb = task
+    mix = sd.make_mixture(seed, n_comp)
+    x = sd.points(mix, sd.STREAM_BASE, start, count)
+    return O.encode_multi_d_adc(x, cb)
+
+
+def _oracle_worker(w, L, k, seconds, nq_max, out_q, procs):
+    """Builds the oracle's own index of the workload, then times its search."""
+    import numpy as np
+
+    import synthdata as sd
+    from oracle import bpq_oracle as O
+    t0 = time.time()
+    mix = sd.make_mixture(w.seed, w.n_comp)
+    learn = sd.points(mix, sd.STREAM_LEARN, 0, min(ORACLE_LEARN, w.n_learn))
+    cb = O.train_multi_d_adc(learn, w.T, w.M, ORACLE_ITERS)
+    step = 250_000
+    tasks = [(w.seed, w.n_comp, s, min(step, w.n_base - s), cb) for s in range(0, w.n_base, step)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        parts = pool.map(_oracle_encode_chunk, tasks)
+    cells = np.concatenate([p[0] for p in parts])
+    codes = np.concatenate([p[1] for p in parts])
+    index = O.OracleIndex(cb=cb, lists=O.build_lists(cells, codes, np.arange(w.n_base), w.T), variant="global",
+                          tables=O.fbpq_tables(cb))
+    build_s = time.time() - t0
+    queries = sd.points(mix, sd.STREAM_QUERY, 0, nq_max)
+    O.search_one(index, queries[0], L, k, "fbpq")  # warm caches
+    done, t1 = 0, time.time()
+    times = []
+    while done < nq_max and (time.time() - t1) < seconds:
+        s = time.time()
+        O.search_one(index, queries[done], L, k, "fbpq")
+        times.append(time.time() - s)
+        done += 1
+    out_q.put(dict(n=done, seconds=sum(times), times=times, build_s=build_s))
+
+
+def run_oracle(w, L, k, seconds, nq_max=200):
+    """Oracle search timing in a spawned process with single-threaded BLAS."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    saved = {v: os.environ.get(v) for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for v in saved:
+        os.environ[v] = "1"
+    procs = max(1, min(16, os.cpu_count() or 1))
+    try:
+        p = ctx.Process(target=_oracle_worker, args=(w, L, k, seconds, nq_max, q, procs))
+        p.start()
+        res = q.get()
+        p.join()
+    finally:
+        for v, val in saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
+    return res
+
+
+def oracle_sample_text(w, L, n):
+    return (f"{n} queries of the {w.name} workload (N={w.n_base}, T={w.T}, M={w.M}) at L={L}, k=100, FBPQ "
+            f"scoring, one at a time on one core, against the oracle's own index (codebooks from "
+            f"{ORACLE_ITERS} Lloyd iterations on {ORACLE_LEARN} learn points)")
+
+
+# ---------------------------------------------------------------------------
+# GPU side
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if device_uuid:
+            cmd += ["-i", device_uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        self.marks = {}
+
+    def mark(self, name):
+        self.marks[name] = time.time()
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        for line in open(self.tmp.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                rows.append(dict(ts=ts, sm=float(parts[2]), smax=float(parts[3]), power=parts[4],
+                                 hw=parts[6], hwt=parts[7], swt=parts[8], swp=parts[9]))
+            except ValueError:
+                continue
+        os.unlink(self.tmp.name)
+        t0, t1 = self.marks.get("start", 0), self.marks.get("end", 1e18)
+        inside = [r for r in rows if t0 - 0.15 <= r["ts"] <= t1 + 0.15]
+        window = "timed region"
+        if not inside:
+            inside, window = rows, "warm-up and timed region"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        reasons = set()
+        for r in inside:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                              ("swp", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in inside), "sm_max_mhz": max(r["smax"] for r in inside),
+                "reasons": sorted(reasons), "samples": len(inside), "window": window}
+
+
+def source_digest(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel_file):
+    """DRAM bytes per launch from the committed ncu summary, if taken on this source."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_1404_1831_gb300", "csrc", kernel_file)
+    ent = rec.get(kernel_file)
+    if ent and ent.get("source_sha256_16") == source_digest(src):
+        return ent
+    return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    torch.backends.cuda.matmul.allow_tf32 = False
+
+    import paper_1404_1831_gb300 as bpq
+    import synthdata as sd
+    from synthdata import device as sdev
+
+    w = workload(args)
+    want_cpu = (rank == 0 and world == 1 and not args.no_cpu_baseline)
+    t_setup = time.time()
+    mix = sd.make_mixture(w.seed, w.n_comp)
+    learn = sdev.points_cuda(mix, sd.STREAM_LEARN, 0, w.n_learn, device=dev)
+    ix = bpq.Index.train(learn, w.T, w.M, iters=w.kmeans_iters)
+    del learn
+    chunk = 2_000_000
+    for s in range(0, w.n_base, chunk):
+        x = sdev.points_cuda(mix, sd.STREAM_BASE, s, min(chunk, w.n_base - s), device=dev)
+        ix.add(x)
+        del x
+    ix.finalize()
+    info = ix.info()
+    nq = w.n_query
+    queries = sdev.points_cuda(mix, sd.STREAM_QUERY, rank * nq, nq, device=dev)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t_setup
+
+    L, k, scorer = args.L, args.k, args.scorer
+    ws = ix.workspace(nq, L, k, scorer)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return ix.search(queries, L, k, scorer, workspace=ws)
+
+    # per-phase kernel times (the same kernels bpq_search launches), CUDA events on this stream
+    cap = int(min(L, max(1, info.n_nonempty)))
+    cells = torch.empty((nq, cap, 4), dtype=torch.int32, device=dev)
+    ncells = torch.empty(nq, dtype=torch.int32, device=dev)
+    npts = torch.empty(nq, dtype=torch.int64, device=dev)
+    tws = ix.workspace(nq, L, k, scorer)
+
+    def phases(reps=3):
+        res = {"tables": [], "traverse": [], "scan": []}
+        for _ in range(reps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            d1, d2, lut = ix.query_tables(queries, lut=(scorer == "fbpq"))
+            ev[1].record(stream)
+            Ls, stride = bpq._L_array(L, nq)
+            bpq._check(bpq.lib().bpq_traverse(ix._h, bpq._ptr(queries), nq, Ls.ctypes.data, stride, cap,
+                                              bpq._ptr(cells), bpq._ptr(ncells), bpq._ptr(npts), bpq._ptr(tws),
+                                              tws.numel(), bpq._stream()))
+            ev[2].record(stream)
+            ix.scan(queries, lut, cells, ncells, k, scorer)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            res["tables"].append(ev[0].elapsed_time(ev[1]))
+            res["traverse"].append(ev[1].elapsed_time(ev[2]))
+            res["scan"].append(ev[2].elapsed_time(ev[3]))
+        return {kk: statistics.median(v) for kk, v in res.items()}
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    ph = phases()
+    cand = int(npts.sum().item())
+    ncell_total = int(ncells.clamp(min=0).sum().item())
+
+    # main timed region
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.mark("start")
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler.mark("end")
+    clocks = sampler.stop()
+    ix.search_status(ws)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = nq * world * args.steps / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    qh = torch.empty((nq, w.dim), dtype=torch.float32).pin_memory()
+    qh.copy_(queries.cpu())
+    idsh = torch.empty((nq, k), dtype=torch.int32).pin_memory()
+    dh = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    Ls, stride = bpq._L_array(L, nq)
+
+    def e2e_step():
+        bpq._check(bpq.lib().bpq_search_host(ix._h, qh.data_ptr(), nq, Ls.ctypes.data, stride, k,
+                                             bpq.SCORERS[scorer], idsh.data_ptr(), dh.data_ptr(), bpq._stream()))
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e = {"value": nq * world * args.steps / (e2e_total / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": nq * w.dim * 4, "d2h_bytes_per_step": nq * k * 8,
+           "ms_per_step": e2e_total / args.steps}
+
+    # roofline of the dominant kernel
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    dominant = max(ph, key=ph.get)
+    scan_bytes = cand * (w.M + 4)
+    trav_bytes = ncell_total * 16 + nq * 2 * w.T * 4
+    tr = recorded_traffic("bpq_scan.cu" if dominant == "scan" else "bpq_traverse.cu")
+    if dominant == "scan":
+        roof = {"kernel": f"{scorer}_scan_kernel", "bound": "hbm", "achieved": scan_bytes / (ph["scan"] / 1e3) / 1e9,
+                "peak": hbm_peak, "unit": "GB/s", "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": scan_bytes, "bytes_per_candidate": w.M + 4,
+                "traffic": tr["bytes_per_launch"] if tr else None}
+    else:
+        roof = {"kernel": f"{dominant}_kernel", "bound": "hbm", "achieved": trav_bytes / (ph[dominant] / 1e3) / 1e9,
+                "peak": hbm_peak, "unit": "GB/s", "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": trav_bytes, "traffic": tr["bytes_per_launch"] if tr else None,
+                "note": "latency-bound (per-query sorts and block reductions); bytes = cell records written + coarse tables read"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "n_base": w.n_base, "dim": w.dim, "T": w.T, "M": w.M, "n_query": nq,
+                      "L": L, "k": k, "scorer": scorer, "codebooks": f"GPU k-means, {w.kmeans_iters} Lloyd "
+                      f"iterations on {w.n_learn} learn points", "l2": "flushed between steps (512 MB write)",
+                      "parallelism": f"replicas x{world} (independent query batches)"},
+           "roofline": roof, "gpu_launches": 4 * args.steps, "clocks": clocks,
+           "phases_ms": ph, "candidates_per_step": cand, "visited_cells_per_step": ncell_total,
+           "index": {"n_points": info.n_points, "n_nonempty_cells": info.n_nonempty, "max_cell": info.max_cell},
+           "e2e": e2e, "setup_s": round(setup_s, 1)}
+
+    if rank == 0 and world == 1 and not args.no_sweep:
+        out["sweep"] = sweep(ix, queries, w, k, flush, stream)
+        out["recall"] = recall(ix, queries, w, mix, L, k, dev)
+
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    del ix
+    torch.cuda.synchronize()
+    if want_cpu:
+        res = run_oracle(w, L, k, args.oracle_seconds)
+        out["cpu_baseline"] = {"value": res["n"] / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": oracle_sample_text(w, L, res["n"]),
+                               "ms_per_query_median": 1e3 * statistics.median(res["times"]),
+                               "oracle_index_build_s": round(res["build_s"], 1)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def sweep(ix, queries, w, k, flush, stream, steps=3):
+    """Queries/s of FBPQ and reconstruction-ADC at each budget of the workload."""
+    import torch
+    res = {}
+    nq = queries.shape[0]
+    for L in w.L:
+        for scorer in ("fbpq", "recon"):
+            ws = ix.workspace(nq, L, k, scorer)
+            ix.search(queries, L, k, scorer, workspace=ws)
+            ms = []
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ix.search(queries, L, k, scorer, workspace=ws)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            res[f"{scorer}_L{L}"] = {"qps": nq / (statistics.median(ms) / 1e3), "ms": statistics.median(ms)}
+        res[f"speedup_L{L}"] = res[f"fbpq_L{L}"]["qps"] / res[f"recon_L{L}"]["qps"]
+    return res
+
+
+def recall(ix, queries, w, mix, L, k, dev, n_gt=1000):
+    """Recall@1/10/100 of the search against exact nearest neighbours (brute force
+    in FP32 with TF32 off: every partial sum is an integer below 2^24, so exact)."""
+    import torch
+
+    from synthdata import device as sdev
+    import synthdata as sd
+    q = queries[:n_gt]
+    qn = (q * q).sum(1, keepdim=True)
+    best = torch.full((n_gt,), float("inf"), device=dev)
+    arg = torch.zeros(n_gt, dtype=torch.int64, device=dev)
+    chunk = 1_000_000
+    for s in range(0, w.n_base, chunk):
+        x = sdev.points_cuda(mix, sd.STREAM_BASE, s, min(chunk, w.n_base - s), device=dev)
+        d = qn - 2.0 * (q @ x.T) + (x * x).sum(1)[None, :]
+        m, a = d.min(1)
+        upd = m < best
+        best = torch.where(upd, m, best)
+        arg = torch.where(upd, a + s, arg)
+    out = {}
+    for scorer in ("fbpq", "recon"):
+        ids, _ = ix.search(q, L, k, scorer)
+        hit = (ids.long() == arg[:, None])
+        out[scorer] = {f"R@{R}": float(hit[:, :R].any(1).float().mean()) for R in (1, 10, 100)}
+    out["n_queries"] = n_gt
+    out["L"] = L
+    return out
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, rank 0 only."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args)
+    per_step = 2
+    total = per_step * (args.steps + args.warmup)
+    res = run_oracle(w, args.L, args.k, seconds=1e9, nq_max=total)
+    times = res["times"][per_step * args.warmup:]
+    seconds = sum(times)
+    value = len(times) / seconds
+    sample = oracle_sample_text(w, args.L, per_step) + f" per step ({args.steps} timed steps, {args.warmup} warm-up)"
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * seconds / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": w.name, "n_base": w.n_base, "dim": w.dim, "T": w.T, "M": w.M, "L": args.L,
+                      "k": args.k, "scorer": "fbpq"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "gpu_launches": 0}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -212,6 +212,19 @@ int bpq_search(const bpq_index* idx, const float* queries_dev, int64_t nq, const
                void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /*
+ * bpq_scan — the scan and top-k stage of bpq_search alone (§2.3.3 reranking,
+ * §3.1, §3.2), on cells written by bpq_traverse: for each query the k smallest
+ * (distance, id) over every point of its ncells_dev[q] visited cells.
+ *  lut_dev: nq x M x 256 tables from bpq_query_tables (FBPQ only, else ignored);
+ *  cells_dev: nq x cap; queries_dev: nq x D (reconstruction scorers);
+ *  counter_dev: one int32 of device scratch (work counter of the persistent
+ *  reconstruction kernels).  Outputs as bpq_search.  Asynchronous on stream.
+ */
+int bpq_scan(const bpq_index* idx, const float* queries_dev, int64_t nq, const float* lut_dev,
+             const bpq_cell* cells_dev, const int32_t* ncells_dev, int32_t cap, int32_t k, int32_t scorer,
+             int32_t* ids_dev, float* dists_dev, int32_t* counter_dev, void* stream);
+
+/*
  * bpq_search_status — synchronizes the stream and returns BPQ_OK, or
  * BPQ_ECAPACITY if any query of the last bpq_search / bpq_traverse on this
  * workspace overflowed a fixed-size buffer.

@@ -61,6 +61,8 @@ _SIGS = {
     "bpq_search": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P,
                                   _P, _P, ctypes.c_size_t, _P]),
     "bpq_search_status": (ctypes.c_int, [_P, _P, _P]),
+    "bpq_scan": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                _P, _P, _P, _P]),
     "bpq_search_host": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                        _P, _P, _P]),
     "bpq_get_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
@@ -122,7 +124,7 @@ class _CudaView:
     """Wraps a raw device pointer for torch.as_tensor (CUDA array interface)."""
 
     def __init__(self, ptr, shape, typestr):
-        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
                                          "version": 2}
 
 
@@ -280,6 +282,21 @@ class Index:
         ws = workspace if workspace is not None else self.workspace(nq, int(Ls.max()), k, scorer)
         _check(lib().bpq_search(self._h, _ptr(q), nq, Ls.ctypes.data, stride, k, SCORERS[scorer], _ptr(ids),
                                 _ptr(dists), _ptr(ws), ws.numel(), _stream(stream)))
+        return ids, dists
+
+    def scan(self, q, lut, cells, ncells, k, scorer="fbpq", stream=None, out=None):
+        """Scan + top-k on traversal output (cells from traverse())."""
+        import torch
+        nq, cap = cells.shape[0], cells.shape[1]
+        if out is None:
+            ids = torch.empty((nq, k), dtype=torch.int32, device=cells.device)
+            dists = torch.empty((nq, k), dtype=torch.float32, device=cells.device)
+        else:
+            ids, dists = out
+        if getattr(self, "_counter", None) is None:
+            self._counter = torch.zeros(1, dtype=torch.int32, device=cells.device)
+        _check(lib().bpq_scan(self._h, _ptr(q), nq, _ptr(lut), _ptr(cells), _ptr(ncells), cap, k, SCORERS[scorer],
+                              _ptr(ids), _ptr(dists), _ptr(self._counter), _stream(stream)))
         return ids, dists
 
     def search_status(self, workspace=None, stream=None):

@@ -143,6 +143,43 @@ void check_searchable(const bpq_index* ix) {
   BPQ_CHECK(ix->n_pending == 0, BPQ_ESTATE, "points were added since the last bpq_finalize");
 }
 
+ScanArgs scan_args(const bpq_index& ix, const float* q, int64_t nq, const float* lut, const bpq_cell* cells,
+                   const int32_t* ncells, int32_t cap, int k, int32_t* ids, float* dists, int32_t* counter) {
+  ScanArgs sa{};
+  sa.cells = cells;
+  sa.ncells = ncells;
+  sa.cap = cap;
+  sa.nq = nq;
+  sa.T = ix.p.T;
+  sa.M = ix.p.M;
+  sa.D = ix.p.D;
+  sa.k = k;
+  sa.lut = lut;
+  sa.X1 = ix.X1.as<float>();
+  sa.X2 = ix.X2.as<float>();
+  sa.queries = q;
+  sa.C1 = ix.C1.as<float>();
+  sa.C2 = ix.C2.as<float>();
+  sa.R = ix.R.as<float>();
+  sa.Q = ix.Q.as<float>();
+  sa.S = ix.S.as<float>();
+  sa.codes = ix.codes.as<uint8_t>();
+  sa.ids = ix.ids.as<int32_t>();
+  sa.out_ids = ids;
+  sa.out_dists = dists;
+  sa.qcounter = counter;
+  sa.sm_count = ix.sm_count;
+  return sa;
+}
+
+void check_scorer(const bpq_index& ix, int scorer) {
+  BPQ_CHECK(scorer >= BPQ_SCORER_FBPQ && scorer <= BPQ_SCORER_HBPQ, BPQ_EINVAL, "bad scorer");
+  if (scorer == BPQ_SCORER_HBPQ)
+    BPQ_CHECK(ix.p.variant == BPQ_VARIANT_LOCAL, BPQ_EINVAL, "the HBPQ scorer needs local codebooks");
+  else
+    BPQ_CHECK(ix.p.variant == BPQ_VARIANT_GLOBAL, BPQ_EINVAL, "FBPQ and reconstruction scorers need global codebooks");
+}
+
 // Runs tables + traversal (+ scan when ids/dists are given) over the queries in
 // chunks that fit the workspace.
 void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride,
@@ -151,21 +188,19 @@ void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t*
   const bool scan = user_cells == nullptr;
   std::vector<int32_t> Lq;
   const int64_t L_max = read_L(L_host, L_stride, nq, &Lq);
-  BPQ_CHECK(q || nq == 0, BPQ_EINVAL, "queries is NULL");
-  BPQ_CHECK(ws, BPQ_EINVAL, "workspace is NULL");
   if (scan) {
     BPQ_CHECK(k >= 1 && k <= MAX_K, BPQ_EINVAL, "k must be in [1, 1024]");
-    BPQ_CHECK(out_ids && out_dists, BPQ_EINVAL, "output pointers are NULL");
-    BPQ_CHECK(scorer >= BPQ_SCORER_FBPQ && scorer <= BPQ_SCORER_HBPQ, BPQ_EINVAL, "bad scorer");
-    if (scorer == BPQ_SCORER_HBPQ)
-      BPQ_CHECK(ix.p.variant == BPQ_VARIANT_LOCAL, BPQ_EINVAL, "the HBPQ scorer needs local codebooks");
-    else
-      BPQ_CHECK(ix.p.variant == BPQ_VARIANT_GLOBAL, BPQ_EINVAL,
-                "FBPQ and reconstruction scorers need global codebooks");
+    check_scorer(ix, scorer);
   } else {
-    BPQ_CHECK(user_cap >= 1 && user_ncells && user_npoints, BPQ_EINVAL, "bad traversal outputs");
+    BPQ_CHECK(user_cap >= 1, BPQ_EINVAL, "cap must be >= 1");
   }
   if (nq <= 0) return;
+  BPQ_CHECK(q, BPQ_EINVAL, "queries is NULL");
+  BPQ_CHECK(ws, BPQ_EINVAL, "workspace is NULL");
+  if (scan)
+    BPQ_CHECK(out_ids && out_dists, BPQ_EINVAL, "output pointers are NULL");
+  else
+    BPQ_CHECK(user_ncells && user_npoints, BPQ_EINVAL, "bad traversal outputs");
   // largest chunk that fits
   int64_t chunk = nq;
   if (layout(ix, chunk, L_max, scorer, scan).total > ws_bytes) {
@@ -216,30 +251,8 @@ void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t*
     }
     launch_traverse(ta, st);
     if (!scan) continue;
-    ScanArgs sa{};
-    sa.cells = ta.cells;
-    sa.ncells = ta.ncells;
-    sa.cap = ta.cap;
-    sa.nq = nc;
-    sa.T = ix.p.T;
-    sa.M = ix.p.M;
-    sa.D = ix.p.D;
-    sa.k = k;
-    sa.lut = lut;
-    sa.X1 = ix.X1.as<float>();
-    sa.X2 = ix.X2.as<float>();
-    sa.queries = qc;
-    sa.C1 = ix.C1.as<float>();
-    sa.C2 = ix.C2.as<float>();
-    sa.R = ix.R.as<float>();
-    sa.Q = ix.Q.as<float>();
-    sa.S = ix.S.as<float>();
-    sa.codes = ix.codes.as<uint8_t>();
-    sa.ids = ix.ids.as<int32_t>();
-    sa.out_ids = out_ids + c0 * k;
-    sa.out_dists = out_dists + c0 * k;
-    sa.qcounter = reinterpret_cast<int32_t*>(w + l.qcounter);
-    sa.sm_count = ix.sm_count;
+    ScanArgs sa = scan_args(ix, qc, nc, lut, ta.cells, ta.ncells, ta.cap, k, out_ids + c0 * k,
+                            out_dists + c0 * k, reinterpret_cast<int32_t*>(w + l.qcounter));
     launch_scan(sa, scorer, st);
   }
 }
@@ -502,7 +515,7 @@ int bpq_traverse(const bpq_index* ix, const float* q, int64_t nq, const int64_t*
   return guard([&] {
     check_searchable(ix);
     BPQ_CHECK(nq >= 0, BPQ_EINVAL, "nq < 0");
-    BPQ_CHECK(cells, BPQ_EINVAL, "cells is NULL");
+    BPQ_CHECK(cells || nq == 0, BPQ_EINVAL, "cells is NULL");
     DeviceGuard dg(ix->device);
     run_queries(*ix, q, nq, L_host, L_stride, 1, BPQ_SCORER_FBPQ, nullptr, nullptr, cells, cap, ncells, npoints,
                 ws, ws_bytes, static_cast<cudaStream_t>(stream));
@@ -516,6 +529,24 @@ int bpq_search(const bpq_index* ix, const float* q, int64_t nq, const int64_t* L
     BPQ_CHECK(nq >= 0, BPQ_EINVAL, "nq < 0");
     DeviceGuard dg(ix->device);
     run_queries(*ix, q, nq, L_host, L_stride, k, scorer, ids, dists, nullptr, 0, nullptr, nullptr, ws, ws_bytes,
+                static_cast<cudaStream_t>(stream));
+  });
+}
+
+int bpq_scan(const bpq_index* ix, const float* q, int64_t nq, const float* lut, const bpq_cell* cells,
+             const int32_t* ncells, int32_t cap, int32_t k, int32_t scorer, int32_t* ids, float* dists,
+             int32_t* counter, void* stream) {
+  return guard([&] {
+    check_searchable(ix);
+    BPQ_CHECK(nq >= 0, BPQ_EINVAL, "nq < 0");
+    if (nq == 0) return;
+    BPQ_CHECK(k >= 1 && k <= MAX_K, BPQ_EINVAL, "k must be in [1, 1024]");
+    check_scorer(*ix, scorer);
+    BPQ_CHECK(cells && ncells && ids && dists && counter && cap >= 1, BPQ_EINVAL, "bad argument");
+    BPQ_CHECK(scorer != BPQ_SCORER_FBPQ || lut, BPQ_EINVAL, "FBPQ needs the query tables");
+    BPQ_CHECK(scorer == BPQ_SCORER_FBPQ || q, BPQ_EINVAL, "reconstruction needs the queries");
+    DeviceGuard dg(ix->device);
+    launch_scan(scan_args(*ix, q, nq, lut, cells, ncells, cap, k, ids, dists, counter), scorer,
                 static_cast<cudaStream_t>(stream));
   });
 }
