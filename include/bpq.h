@@ -240,6 +240,34 @@ int bpq_search_host(bpq_index* idx, const float* queries_host, int64_t nq, const
                     int64_t L_stride, int32_t k, int32_t scorer, int32_t* ids_host,
                     float* dists_host, void* stream);
 
+/*
+ * bpq_search_noalloc — bpq_search without any device allocation, for callers
+ * that cannot call cudaMalloc: programs whose device memory is all owned by
+ * their own pool or budget, and latency-critical loops where a cudaMalloc /
+ * cudaFree (which can synchronize the whole device) is not acceptable.  The
+ * paper has no counterpart: this is a deployment convenience of this library.
+ *  Same arguments and results as bpq_search, minus the workspace: the scratch
+ *  data (query tables, visited-cell lists, counters) live in one fixed array of
+ *  BPQ_NOALLOC_SCRATCH_BYTES of device memory inside the library, reserved on
+ *  every GPU that loads the library until the process exits.
+ *  A batch fits if bpq_search_workspace_size(idx, nq, max L, k, scorer) <=
+ *  BPQ_NOALLOC_SCRATCH_BYTES; a larger batch returns BPQ_ECAPACITY before any
+ *  GPU work (split the batch).  status_dev (may be NULL): one int32 of device
+ *  memory that receives 0, or 1 if a query overflowed the traversal band.
+ *  The first call on a device looks up the array's device address (one-time
+ *  set-up), so make that first call before any stream capture.  Every call
+ *  shares the array and it keeps the previous call's contents; calls whose GPU
+ *  work overlaps (other streams, other threads) race on it, so order them.
+ *  Per-query budgets (L_stride == 1) are copied from host memory with
+ *  cudaMemcpyAsync.  Failures are reported by the return code only
+ *  (bpq_last_error is not updated): BPQ_EINVAL, BPQ_ESTATE, BPQ_ECAPACITY,
+ *  BPQ_ECUDA as for bpq_search.  Asynchronous on stream.
+ */
+#define BPQ_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20) /* 32 MiB */
+int bpq_search_noalloc(const bpq_index* idx, const float* queries_dev, int64_t nq, const int64_t* L_host,
+                       int64_t L_stride, int32_t k, int32_t scorer, int32_t* ids_dev, float* dists_dev,
+                       int32_t* status_dev, void* stream);
+
 /* bpq_info / bpq_arrays — sizes and read-only device views (see the structs). */
 int bpq_get_info(const bpq_index* idx, bpq_info* out);
 int bpq_get_arrays(const bpq_index* idx, bpq_arrays* out);

@@ -65,6 +65,8 @@ _SIGS = {
                                 _P, _P, _P, _P]),
     "bpq_search_host": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                        _P, _P, _P]),
+    "bpq_search_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.c_int32, _P, _P, _P, _P]),
     "bpq_get_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
     "bpq_get_arrays": (ctypes.c_int, [_P, ctypes.POINTER(Arrays)]),
     "bpq_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
@@ -297,6 +299,22 @@ class Index:
             self._counter = torch.zeros(1, dtype=torch.int32, device=cells.device)
         _check(lib().bpq_scan(self._h, _ptr(q), nq, _ptr(lut), _ptr(cells), _ptr(ncells), cap, k, SCORERS[scorer],
                               _ptr(ids), _ptr(dists), _ptr(self._counter), _stream(stream)))
+        return ids, dists
+
+    def search_noalloc(self, q, L, k, scorer="fbpq", stream=None, status=None):
+        """bpq_search_noalloc: the search with the library's built-in scratch array
+        instead of a workspace, for callers that must not allocate device memory.
+        Raises BpqError with the return code on failure (e.g. ECAPACITY for a
+        batch larger than the built-in scratch)."""
+        import torch
+        nq = q.shape[0]
+        Ls, stride = _L_array(L, nq)
+        ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=q.device)
+        rc = lib().bpq_search_noalloc(self._h, _ptr(q), nq, Ls.ctypes.data, stride, k, SCORERS[scorer], _ptr(ids),
+                                      _ptr(dists), _ptr(status), _stream(stream))
+        if rc != BPQ_OK:
+            raise BpqError(rc, "bpq_search_noalloc failed")
         return ids, dists
 
     def search_status(self, workspace=None, stream=None):
