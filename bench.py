@@ -47,6 +47,7 @@ def parse_args():
     ap.add_argument("--k", type=int, default=100)
     ap.add_argument("--scorer", default="fbpq")
     ap.add_argument("--n-base", type=int, default=None, help="override the point count (testing only)")
+    ap.add_argument("--n-query", type=int, default=None, help="override the queries per step (profiling only)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the L / scorer sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
@@ -60,6 +61,8 @@ def workload(args):
     w = sd.SIFT10M
     if args.n_base:
         w = dataclasses.replace(w, n_base=args.n_base)
+    if args.n_query:
+        w = dataclasses.replace(w, n_query=args.n_query)
     return w
 
 
