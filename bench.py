@@ -277,7 +277,7 @@ def run_ours(args):
             flush.zero_()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             ev[0].record(stream)
-            d1, d2, lut = ix.query_tables(queries, lut=(scorer == "fbpq"))
+            d1, d2, lut = ix.query_tables(queries, lut=scorer.startswith("fbpq"))
             ev[1].record(stream)
             Ls, stride = bpq._L_array(L, nq)
             bpq._check(bpq.lib().bpq_traverse(ix._h, bpq._ptr(queries), nq, Ls.ctypes.data, stride, cap,
@@ -426,7 +426,7 @@ def sweep(ix, queries, w, k, flush, stream, steps=3):
     res = {}
     nq = queries.shape[0]
     for L in w.L:
-        for scorer in ("fbpq", "recon"):
+        for scorer in ("fbpq", "fbpq_tables", "recon"):
             ws = ix.workspace(nq, L, k, scorer)
             ix.search(queries, L, k, scorer, workspace=ws)
             ms = []
@@ -441,6 +441,7 @@ def sweep(ix, queries, w, k, flush, stream, steps=3):
                 ms.append(e0.elapsed_time(e1))
             res[f"{scorer}_L{L}"] = {"qps": nq / (statistics.median(ms) / 1e3), "ms": statistics.median(ms)}
         res[f"speedup_L{L}"] = res[f"fbpq_L{L}"]["qps"] / res[f"recon_L{L}"]["qps"]
+        res[f"speedup_tables_L{L}"] = res[f"fbpq_tables_L{L}"]["qps"] / res[f"recon_L{L}"]["qps"]
     return res
 
 

@@ -55,11 +55,15 @@ enum {
 
 /* Candidate scorers. */
 enum {
-  BPQ_SCORER_FBPQ = 0,  /* Eq. 8 with Eq. 9: per-query lookup tables reused in every
-                           cell, O(M) per candidate (§3.1) */
+  BPQ_SCORER_FBPQ = 0,  /* Eq. 8: per-query lookup tables reused in every cell (§3.1);
+                           the query-independent cross term 2<c_ij, r> of Eq. 9 is
+                           precomputed per point at index build, so a candidate
+                           costs M table lookups plus one stored scalar */
   BPQ_SCORER_RECON = 1, /* Multi-D-ADC: per-cell query displacement and explicit
                            reconstruction, O(D) per candidate (§2.3.3) */
-  BPQ_SCORER_HBPQ = 2   /* HBPQ: reconstruction with local codebooks, O(D) (§3.2) */
+  BPQ_SCORER_HBPQ = 2,  /* HBPQ: reconstruction with local codebooks, O(D) (§3.2) */
+  BPQ_SCORER_FBPQ_TABLES = 3 /* Eq. 8 with Eq. 9 evaluated from the T*M*K cross tables of
+                           §3.3 at query time: 2M table lookups per candidate */
 };
 
 typedef struct bpq_index bpq_index;
@@ -94,6 +98,8 @@ typedef struct {
   const uint32_t* offsets; /* T*T + 1 start positions of the cells (§2.3.2) */
   const uint8_t* codes; /* n_points x M, cell-contiguous */
   const int32_t* ids;   /* n_points, ascending inside each cell */
+  const float* cross;   /* n_points: 2<c_ij, r> of each point (Eq. 9 cross term; global
+                           variant, else NULL) */
 } bpq_arrays;
 
 /* One visited cell, as bpq_traverse writes it. */
@@ -199,7 +205,7 @@ int bpq_traverse(const bpq_index* idx, const float* queries_dev, int64_t nq, con
  * ||q - x^||^2 (Eq. 8), ascending, ties by id; slots beyond the candidate count
  * hold id -1 and distance +inf.
  *  queries_dev: nq x D float32; k in [1, 1024]; scorer: BPQ_SCORER_*
- *  (FBPQ and RECON need the global variant, HBPQ the local one).
+ *  (FBPQ, FBPQ_TABLES and RECON need the global variant, HBPQ the local one).
  *  ids_dev: nq x k int32; dists_dev: nq x k float32.
  *  workspace_dev: at least bpq_search_workspace_size(idx, nq, max L, k, scorer)
  *  bytes, or fewer: queries are then processed in chunks that fit (at least one
@@ -215,7 +221,7 @@ int bpq_search(const bpq_index* idx, const float* queries_dev, int64_t nq, const
  * bpq_scan — the scan and top-k stage of bpq_search alone (§2.3.3 reranking,
  * §3.1, §3.2), on cells written by bpq_traverse: for each query the k smallest
  * (distance, id) over every point of its ncells_dev[q] visited cells.
- *  lut_dev: nq x M x 256 tables from bpq_query_tables (FBPQ only, else ignored);
+ *  lut_dev: nq x M x 256 tables from bpq_query_tables (FBPQ scorers, else ignored);
  *  cells_dev: nq x cap; queries_dev: nq x D (reconstruction scorers);
  *  counter_dev: one int32 of device scratch (work counter of the persistent
  *  reconstruction kernels).  Outputs as bpq_search.  Asynchronous on stream.

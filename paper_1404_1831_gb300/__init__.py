@@ -18,7 +18,7 @@ BPQ_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "EIO", -4: "ECORRUPT", -5: "ETIMEOUT", -6: "ECUDA", -7: "ECAPACITY",
           -8: "ESTATE"}
 VARIANT_GLOBAL, VARIANT_LOCAL = 0, 1
-SCORERS = {"fbpq": 0, "recon": 1, "hbpq": 2}
+SCORERS = {"fbpq": 0, "recon": 1, "hbpq": 2, "fbpq_tables": 3}
 
 
 class BpqError(RuntimeError):
@@ -38,7 +38,8 @@ class Info(ctypes.Structure):
 
 
 class Arrays(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_void_p) for n in ("C1", "C2", "R", "Q", "S", "X1", "X2", "offsets", "codes", "ids")]
+    _fields_ = [(n, ctypes.c_void_p) for n in ("C1", "C2", "R", "Q", "S", "X1", "X2", "offsets", "codes", "ids",
+                                                "cross")]
 
 
 CELL_DTYPE = np.dtype([("cell", "<u4"), ("begin", "<u4"), ("count", "<u4"), ("key", "<f4")])
@@ -228,7 +229,8 @@ class Index:
         shapes = {"C1": ((p.T, h), "<f4"), "C2": ((p.T, h), "<f4"), "R": ((p.M, 256, s), "<f4"),
                   "Q": ((p.T, m2, 256, s), "<f4"), "S": ((p.T, m2, 256, s), "<f4"),
                   "X1": ((p.T, m2, 256), "<f4"), "X2": ((p.T, m2, 256), "<f4"),
-                  "offsets": ((p.T * p.T + 1,), "<u4"), "codes": ((n, p.M), "|u1"), "ids": ((n,), "<i4")}
+                  "offsets": ((p.T * p.T + 1,), "<u4"), "codes": ((n, p.M), "|u1"), "ids": ((n,), "<i4"),
+                  "cross": ((n,), "<f4")}
         out = {}
         dev = torch.device("cuda", self.device)
         for name, (shape, ts) in shapes.items():

@@ -90,6 +90,8 @@ size_t cb_floats_local(const bpq_params& p) { return (size_t)p.T * (p.M / 2) * K
 // ---------------------------------------------------------------------------
 // Workspace layout for a chunk of nq queries.
 // ---------------------------------------------------------------------------
+bool uses_lut(int scorer);
+
 struct Layout {
   size_t status, qcounter, L, d1, d2, lut, cells, ncells, npoints, total;
   int64_t cap;
@@ -111,7 +113,7 @@ Layout layout(const bpq_index& ix, int64_t nq, int64_t L_max, int scorer, bool w
   l.d2 = o;
   o = align_up(o + (size_t)nq * ix.p.T * 4);
   l.lut = o;
-  if (scorer == BPQ_SCORER_FBPQ && with_cells) o = align_up(o + (size_t)nq * ix.p.M * KSUB * 4);
+  if (uses_lut(scorer) && with_cells) o = align_up(o + (size_t)nq * ix.p.M * KSUB * 4);
   l.cap = std::max<int64_t>(1, std::min<int64_t>(L_max, std::max<int64_t>(ix.n_nonempty, 1)));
   l.cells = o;
   if (with_cells) o = align_up(o + (size_t)nq * l.cap * sizeof(bpq_cell));
@@ -157,6 +159,7 @@ ScanArgs scan_args(const bpq_index& ix, const float* q, int64_t nq, const float*
   sa.lut = lut;
   sa.X1 = ix.X1.as<float>();
   sa.X2 = ix.X2.as<float>();
+  sa.cross = ix.cross.as<float>();
   sa.queries = q;
   sa.C1 = ix.C1.as<float>();
   sa.C2 = ix.C2.as<float>();
@@ -172,8 +175,10 @@ ScanArgs scan_args(const bpq_index& ix, const float* q, int64_t nq, const float*
   return sa;
 }
 
+bool uses_lut(int scorer) { return scorer == BPQ_SCORER_FBPQ || scorer == BPQ_SCORER_FBPQ_TABLES; }
+
 void check_scorer(const bpq_index& ix, int scorer) {
-  BPQ_CHECK(scorer >= BPQ_SCORER_FBPQ && scorer <= BPQ_SCORER_HBPQ, BPQ_EINVAL, "bad scorer");
+  BPQ_CHECK(scorer >= BPQ_SCORER_FBPQ && scorer <= BPQ_SCORER_FBPQ_TABLES, BPQ_EINVAL, "bad scorer");
   if (scorer == BPQ_SCORER_HBPQ)
     BPQ_CHECK(ix.p.variant == BPQ_VARIANT_LOCAL, BPQ_EINVAL, "the HBPQ scorer needs local codebooks");
   else
@@ -221,7 +226,7 @@ void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t*
     const float* qc = q + c0 * ix.p.D;
     float* d1 = reinterpret_cast<float*>(w + l.d1);
     float* d2 = reinterpret_cast<float*>(w + l.d2);
-    float* lut = (scan && scorer == BPQ_SCORER_FBPQ) ? reinterpret_cast<float*>(w + l.lut) : nullptr;
+    float* lut = (scan && uses_lut(scorer)) ? reinterpret_cast<float*>(w + l.lut) : nullptr;
     launch_query_tables(ix, qc, nc, d1, d2, lut, st);
     TraverseArgs ta{};
     ta.d1 = d1;
@@ -347,6 +352,7 @@ bpq_index* load_file(const char* path, int device) {
     ix->n_nonempty = nonempty;
     ix->max_cell = maxc;
     build_fbpq_tables(*ix, 0);
+    build_point_cross(*ix, 0);
     BPQ_CUDA(cudaDeviceSynchronize());
   } catch (...) {
     delete ix;
@@ -543,8 +549,8 @@ int bpq_scan(const bpq_index* ix, const float* q, int64_t nq, const float* lut, 
     BPQ_CHECK(k >= 1 && k <= MAX_K, BPQ_EINVAL, "k must be in [1, 1024]");
     check_scorer(*ix, scorer);
     BPQ_CHECK(cells && ncells && ids && dists && counter && cap >= 1, BPQ_EINVAL, "bad argument");
-    BPQ_CHECK(scorer != BPQ_SCORER_FBPQ || lut, BPQ_EINVAL, "FBPQ needs the query tables");
-    BPQ_CHECK(scorer == BPQ_SCORER_FBPQ || q, BPQ_EINVAL, "reconstruction needs the queries");
+    BPQ_CHECK(!uses_lut(scorer) || lut, BPQ_EINVAL, "FBPQ needs the query tables");
+    BPQ_CHECK(uses_lut(scorer) || q, BPQ_EINVAL, "reconstruction needs the queries");
     DeviceGuard dg(ix->device);
     launch_scan(scan_args(*ix, q, nq, lut, cells, ncells, cap, k, ids, dists, counter), scorer,
                 static_cast<cudaStream_t>(stream));
@@ -597,7 +603,7 @@ int bpq_get_info(const bpq_index* ix, bpq_info* out) {
     out->max_cell = ix->max_cell;
     out->device_bytes = (int64_t)(ix->C1.bytes + ix->C2.bytes + ix->R.bytes + ix->Q.bytes + ix->S.bytes +
                                   ix->X1.bytes + ix->X2.bytes + ix->offsets.bytes + ix->codes.bytes +
-                                  ix->ids.bytes + ix->pend_cells.bytes + ix->pend_codes.bytes +
+                                  ix->ids.bytes + ix->cross.bytes + ix->pend_cells.bytes + ix->pend_codes.bytes +
                                   ix->pend_ids.bytes);
     out->params = ix->p;
   });
@@ -616,6 +622,7 @@ int bpq_get_arrays(const bpq_index* ix, bpq_arrays* out) {
     out->offsets = ix->offsets.as<uint32_t>();
     out->codes = ix->codes.as<uint8_t>();
     out->ids = ix->ids.as<int32_t>();
+    out->cross = ix->cross.as<float>();
   });
 }
 

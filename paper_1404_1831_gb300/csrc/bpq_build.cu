@@ -343,6 +343,27 @@ __global__ void gather_lists_kernel(const uint64_t* keys, const uint32_t* vals, 
   atomicAdd(counts + (k >> 32), 1u);
 }
 
+// Per-point cross term of Eq. 9: sum_{k<M/2} X1[i][k][r_k] + sum_{k>=M/2} X2[j][k-M/2][r_k]
+// = 2<[c^1_i; c^2_j], r>, for the point at list position p (its cell from the offsets).
+__global__ void point_cross_kernel(const uint32_t* offsets, int64_t ncells, const uint8_t* codes, int M, int T,
+                                   const float* X1, const float* X2, int64_t n, float* out) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int64_t lo = 0, hi = ncells;  // last cell with offsets[c] <= p
+  while (hi - lo > 1) {
+    int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)offsets[mid] <= p) lo = mid; else hi = mid;
+  }
+  const int64_t i = lo / T, j = lo % T;
+  const int m2 = M / 2;
+  float acc = 0.f;
+  for (int k = 0; k < M; ++k) {
+    const int b = codes[p * M + k];
+    acc += (k < m2) ? X1[(i * m2 + k) * KSUB + b] : X2[(j * m2 + k - m2) * KSUB + b];
+  }
+  out[p] = acc;
+}
+
 __global__ void cell_stats_kernel(const uint32_t* counts, int64_t ncells, unsigned long long* nonempty,
                                   unsigned int* maxc) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -442,6 +463,20 @@ bool ids_nonnegative(const int32_t* ids, int64_t n, cudaStream_t st) {
   return bad == 0;
 }
 
+void build_point_cross(bpq_index& ix, cudaStream_t st) {
+  const int64_t n = ix.n_points;
+  if (ix.p.variant != BPQ_VARIANT_GLOBAL || n == 0) {
+    ix.cross.release();
+    return;
+  }
+  ix.cross.alloc(n * 4);
+  point_cross_kernel<<<blocks_for(n), NTB, 0, st>>>(ix.offsets.as<uint32_t>(), (int64_t)ix.p.T * ix.p.T,
+                                                    ix.codes.as<uint8_t>(), ix.p.M, ix.p.T, ix.X1.as<float>(),
+                                                    ix.X2.as<float>(), n, ix.cross.as<float>());
+  check_launch("point cross terms");
+  BPQ_CUDA(cudaStreamSynchronize(st));
+}
+
 void finalize_lists(bpq_index& ix, cudaStream_t st) {
   const int64_t n_old = ix.n_points, n_new = ix.n_pending, n = n_old + n_new;
   const int T = ix.p.T, M = ix.p.M;
@@ -500,6 +535,7 @@ void finalize_lists(bpq_index& ix, cudaStream_t st) {
   ix.pend_cells.release();
   ix.pend_codes.release();
   ix.pend_ids.release();
+  build_point_cross(ix, st);
 }
 
 void train_codebooks(bpq_index& ix, const float* learn, int64_t n, cudaStream_t st) {

@@ -159,6 +159,7 @@ struct bpq_index {
   int64_t n_added = 0;  // for default ids
   // finalized lists
   bpq::DevBuf offsets, codes, ids;
+  bpq::DevBuf cross;  // per point 2<c_ij, r> (global variant)
   int64_t n_points = 0, n_nonempty = 0, max_cell = 0;
   // workspace owned by bpq_search_host
   bpq::DevBuf host_ws, host_q, host_ids, host_dists;
@@ -204,6 +205,7 @@ struct ScanArgs {
   const float* lut;      // nq x M x 256 (FBPQ)
   const float* X1;       // T x M/2 x 256
   const float* X2;
+  const float* cross;    // per point 2<c_ij, r> (FBPQ)
   const float* queries;  // nq x D (recon / hbpq)
   const float* C1;
   const float* C2;
@@ -226,5 +228,6 @@ void launch_encode(const bpq_index& ix, const float* x, int64_t n, int32_t* cell
 void finalize_lists(bpq_index& ix, cudaStream_t st);
 void train_codebooks(bpq_index& ix, const float* learn, int64_t n, cudaStream_t st);
 void fill_sequential_ids(int32_t* ids, int64_t n, int64_t start, cudaStream_t st);
+void build_point_cross(bpq_index& ix, cudaStream_t st);  // per-point Eq. 9 cross terms
 
 }  // namespace bpq

@@ -61,7 +61,8 @@ Offsets plan(const bpq_index& ix, int64_t nq, int64_t L_max, int scorer) {
   o.L = take((size_t)nq * 4);
   o.d1 = take((size_t)nq * ix.p.T * 4);
   o.d2 = take((size_t)nq * ix.p.T * 4);
-  o.lut = take(scorer == BPQ_SCORER_FBPQ ? (size_t)nq * ix.p.M * bpq::KSUB * 4 : 0);
+  const bool lut = scorer == BPQ_SCORER_FBPQ || scorer == BPQ_SCORER_FBPQ_TABLES;
+  o.lut = take(lut ? (size_t)nq * ix.p.M * bpq::KSUB * 4 : 0);
   o.cells = take((size_t)nq * o.cap * sizeof(bpq_cell));
   o.ncells = take((size_t)nq * 4);
   o.npoints = take((size_t)nq * 8);
@@ -82,7 +83,7 @@ extern "C" int bpq_search_noalloc(const bpq_index* ix, const float* queries_dev,
   if (ix->n_pending != 0) return fail(BPQ_ESTATE, "points were added since the last bpq_finalize");
   if (nq < 0) return fail(BPQ_EINVAL, "nq < 0");
   if (k < 1 || k > bpq::MAX_K) return fail(BPQ_EINVAL, "k must be in [1, 1024]");
-  if (scorer < BPQ_SCORER_FBPQ || scorer > BPQ_SCORER_HBPQ) return fail(BPQ_EINVAL, "bad scorer");
+  if (scorer < BPQ_SCORER_FBPQ || scorer > BPQ_SCORER_FBPQ_TABLES) return fail(BPQ_EINVAL, "bad scorer");
   if ((scorer == BPQ_SCORER_HBPQ) != (ix->p.variant == BPQ_VARIANT_LOCAL))
     return fail(BPQ_EINVAL, "scorer does not match the codebook variant");
   if (!L_host || (L_stride != 0 && L_stride != 1)) return fail(BPQ_EINVAL, "L must be given with stride 0 or 1");
@@ -107,7 +108,8 @@ extern "C" int bpq_search_noalloc(const bpq_index* ix, const float* queries_dev,
     BPQ_CUDA(cudaMemsetAsync(w + o.status, 0, 4, st));
     float* d1 = reinterpret_cast<float*>(w + o.d1);
     float* d2 = reinterpret_cast<float*>(w + o.d2);
-    float* lut = scorer == BPQ_SCORER_FBPQ ? reinterpret_cast<float*>(w + o.lut) : nullptr;
+    const bool uses_lut = scorer == BPQ_SCORER_FBPQ || scorer == BPQ_SCORER_FBPQ_TABLES;
+    float* lut = uses_lut ? reinterpret_cast<float*>(w + o.lut) : nullptr;
     bpq::launch_query_tables(*ix, queries_dev, nq, d1, d2, lut, st);
     bpq::TraverseArgs ta{};
     ta.d1 = d1;
@@ -148,6 +150,7 @@ extern "C" int bpq_search_noalloc(const bpq_index* ix, const float* queries_dev,
     sa.lut = lut;
     sa.X1 = ix->X1.as<float>();
     sa.X2 = ix->X2.as<float>();
+    sa.cross = ix->cross.as<float>();
     sa.queries = queries_dev;
     sa.C1 = ix->C1.as<float>();
     sa.C2 = ix->C2.as<float>();

@@ -159,8 +159,10 @@ __device__ int block_excl_scan(int x, int* tmp, int* total) {
 
 // ---------------------------------------------------------------------------
 // FBPQ scan: one CTA per query.
+//  POINT = true : per-point cross term (one coalesced float per candidate)
+//  POINT = false: cross terms gathered from the X1 / X2 tables (2M lookups)
 // ---------------------------------------------------------------------------
-template <int M, int KP>
+template <int M, int KP, bool POINT>
 __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
   constexpr int NT = 256, NW = NT / 32, CH = NT, ILP = 4, M2 = M / 2;
   using TK = WarpTopK<KP>;
@@ -174,12 +176,15 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
   __shared__ int c_pref[CH + 1];
   __shared__ int scan_tmp[NW + 1];
   __shared__ unsigned long long thr;
-  const int warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = a.k;
 
   for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
     __syncthreads();
-    for (int t = threadIdx.x; t < M * KSUB; t += NT) lut[t] = a.lut[q * M * KSUB + t];
+    {
+      const float4* src = reinterpret_cast<const float4*>(a.lut + q * M * KSUB);
+      for (int t = threadIdx.x; t < M * KSUB / 4; t += NT) reinterpret_cast<float4*>(lut)[t] = src[t];
+    }
     TK tk;
     tk.init(areas + warp * TK::AREA);
     if (threadIdx.x == 0) thr = EMPTY;
@@ -190,11 +195,13 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
       int cnt = 0;
       if ((int)threadIdx.x < nch) {
         bpq_cell c = cl[cs + threadIdx.x];
-        uint32_t i = c.cell / (uint32_t)a.T, j = c.cell % (uint32_t)a.T;
         c_beg[threadIdx.x] = c.begin;
         c_key[threadIdx.x] = c.key;
-        c_x1[threadIdx.x] = i * M2 * KSUB;
-        c_x2[threadIdx.x] = j * M2 * KSUB;
+        if (!POINT) {
+          uint32_t i = c.cell / (uint32_t)a.T, j = c.cell % (uint32_t)a.T;
+          c_x1[threadIdx.x] = i * M2 * KSUB;
+          c_x2[threadIdx.x] = j * M2 * KSUB;
+        }
         cnt = (int)c.count;
       }
       int total;
@@ -204,17 +211,29 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
       const int P = total;
       for (int base = 0; base < P; base += NT * ILP) {
         Code<M> code[ILP];
+        float pc[ILP];
         int cidx[ILP];
         uint32_t pos[ILP];
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
-          const int f = base + u * NT + threadIdx.x;
+          // the lanes of a warp hold 32 consecutive candidates: one search for the
+          // warp's first candidate, then a search in the next 32 cells at most
+          const int fw = base + u * NT + warp * 32;
+          const int f = fw + lane;
           cidx[u] = -1;
-          if (f < P) {
-            const int c = find_cell(c_pref, nch, f);
-            cidx[u] = c;
-            pos[u] = c_beg[c] + (uint32_t)(f - c_pref[c]);
-            code[u].load(a.codes, pos[u]);
+          if (fw < P) {
+            const int c0 = find_cell(c_pref, nch, fw);
+            if (f < P) {
+              int lo = c0, hi = min(nch, c0 + 32);
+              while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (c_pref[mid] <= f) lo = mid; else hi = mid;
+              }
+              cidx[u] = lo;
+              pos[u] = c_beg[lo] + (uint32_t)(f - c_pref[lo]);
+              code[u].load(a.codes, pos[u]);
+              if (POINT) pc[u] = __ldg(a.cross + pos[u]);
+            }
           }
         }
         const unsigned long long th = *(volatile unsigned long long*)&thr;
@@ -225,14 +244,21 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
           uint64_t comp = 0;
           if (cidx[u] >= 0) {
             const int c = cidx[u];
-            const float* x1 = a.X1 + c_x1[c];
-            const float* x2 = a.X2 + c_x2[c];
-            float part = 0.f;
+            float part;
+            if (POINT) {
+              part = pc[u];
 #pragma unroll
-            for (int kk = 0; kk < M; ++kk) {
-              const uint32_t b = code[u].byte(kk);
-              const float xv = (kk < M2) ? __ldg(x1 + kk * KSUB + b) : __ldg(x2 + (kk - M2) * KSUB + b);
-              part += lut[kk * KSUB + b] + xv;
+              for (int kk = 0; kk < M; ++kk) part += lut[kk * KSUB + code[u].byte(kk)];
+            } else {
+              part = 0.f;
+              const float* x1 = a.X1 + c_x1[c];
+              const float* x2 = a.X2 + c_x2[c];
+#pragma unroll
+              for (int kk = 0; kk < M; ++kk) {
+                const uint32_t b = code[u].byte(kk);
+                const float xv = (kk < M2) ? __ldg(x1 + kk * KSUB + b) : __ldg(x2 + (kk - M2) * KSUB + b);
+                part += lut[kk * KSUB + b] + xv;
+              }
             }
             const float dist = c_key[c] + part;
             const uint32_t o = f2ord(dist);
@@ -378,13 +404,14 @@ __global__ void __launch_bounds__(NW * 32) recon_scan_kernel(ScanArgs a) {
   }
 }
 
-template <int M, int KP>
+template <int M, int KP, bool POINT>
 void run_fbpq(const ScanArgs& a, cudaStream_t st) {
   using TK = WarpTopK<KP>;
   const size_t smem = (size_t)M * KSUB * 4 + (size_t)8 * TK::AREA * 8;
-  BPQ_CUDA(cudaFuncSetAttribute(fbpq_scan_kernel<M, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  auto kern = fbpq_scan_kernel<M, KP, POINT>;
+  BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
-  fbpq_scan_kernel<M, KP><<<grid, 256, smem, st>>>(a);
+  kern<<<grid, 256, smem, st>>>(a);
   check_launch("fbpq scan kernel");
 }
 
@@ -405,8 +432,11 @@ void run_recon(const ScanArgs& a, cudaStream_t st) {
 
 template <int M, int SUB, int KP>
 void dispatch_scorer(const ScanArgs& a, int scorer, cudaStream_t st) {
-  if (scorer == BPQ_SCORER_FBPQ)
-    run_fbpq<M, KP>(a, st);
+  if (scorer == BPQ_SCORER_FBPQ) {
+    BPQ_CHECK(a.cross || a.nq == 0, BPQ_ESTATE, "FBPQ needs the per-point cross terms (global variant)");
+    run_fbpq<M, KP, true>(a, st);
+  } else if (scorer == BPQ_SCORER_FBPQ_TABLES)
+    run_fbpq<M, KP, false>(a, st);
   else if (scorer == BPQ_SCORER_RECON)
     run_recon<M, SUB, KP, false>(a, st);
   else

@@ -5,13 +5,15 @@
 // the visited cells hold l points.  A sequential heap is a poor fit for a GPU,
 // so this kernel computes the same visit order in bands:
 //
-//   1. sort d1 and d2 (with their indices) in shared memory: s1, p1 and s2, p2;
-//      every row u of the (u, v) rank grid then has keys s1[u] + s2[v] that are
-//      non-decreasing in v, and rows are ordered by s1[u];
+//   1. sort d2 (with its indices) in shared memory: s2, p2; every row i then has
+//      keys d1[i] + s2[v] that are non-decreasing in v, and the cells of row i
+//      visited so far are the columns v < vlo[i] (rows need no order);
 //   2. a band is every cell whose key lies in (tau_lo, tau_hi]; tau_hi is found
-//      by bisection on the number of cells with key <= tau (a per-row binary
-//      search, summed over the block) so that the band holds at most a fixed
-//      number of cells;
+//      by bisection on the number of cells with key <= tau (a binary search in
+//      the rows whose next cell is <= tau, summed over the block), stopping
+//      once the band holds between half the target and the target; the first
+//      band targets L / rho cells (rho = mean points per non-empty cell) and
+//      every further band twice the previous one, up to a fixed capacity;
 //   3. the band's cells are enumerated row by row, their point counts read from
 //      the cell offsets, empty cells dropped, and the rest sorted by
 //      (key, cell id);
@@ -96,19 +98,17 @@ __device__ long long block_incl_scan(long long x, Red& r, long long* total) {
 }
 
 struct Lists {
-  float* s1;
-  float* s2;
-  int* p1;
-  int* p2;
-  int* vlo;
+  const float* s1;  // d1 in row order (unsorted)
+  float* s2;        // d2 sorted ascending
+  int* p2;          // column of s2[v]
+  int* vlo;         // per row: columns already emitted (keys <= tau_lo)
   int* vhi;
-  int* rowpref;  // T + 1
+  int* rowpref;     // T + 1
   uint64_t* band;
   int T;
 };
 
-// Number of v in [from, T) ... i.e. the count of cells (u, v), v < T, with key <= h,
-// knowing that the first `from` of them qualify.
+// Columns v of row u with key <= h, knowing that the first `from` qualify.
 __device__ __forceinline__ int row_count(const Lists& S, int u, int from, uint32_t h) {
   const float a = S.s1[u];
   int lo = from, hi = S.T;  // first v with key > h lies in [lo, hi]
@@ -122,12 +122,12 @@ __device__ __forceinline__ int row_count(const Lists& S, int u, int from, uint32
   return lo;
 }
 
-// Cells with key <= h (all rows), given that row u already has vlo[u] such cells.
-__device__ long long count_cells(const Lists& S, uint32_t h, Red& r) {
+// Cells with tau_lo < key <= h (all rows).  Rows whose next cell is above h add nothing.
+__device__ long long count_band(const Lists& S, uint32_t h, Red& r) {
   long long c = 0;
   for (int u = threadIdx.x; u < S.T; u += NT) {
-    if (f2ord(__fadd_rn(S.s1[u], S.s2[0])) > h) break;  // rows are sorted by s1
-    c += row_count(S, u, S.vlo[u], h);
+    const int v = S.vlo[u];
+    if (v < S.T && f2ord(__fadd_rn(S.s1[u], S.s2[v])) <= h) c += row_count(S, u, v + 1, h) - v;
   }
   return block_sum(c, r);
 }
@@ -141,16 +141,16 @@ __global__ void __launch_bounds__(NT) traverse_kernel(TraverseArgs a) {
   const int T = a.T;
   int TP = 1;
   while (TP < T) TP <<= 1;
-  // shared layout: [keys / band union][s1 s2 p1 p2 vlo vhi][rowpref]
+  // shared layout: [d2 sort keys / band union][s1 s2 p2 vlo vhi][rowpref]
   uint64_t* keys = reinterpret_cast<uint64_t*>(smem);
-  const size_t union_bytes = max((size_t)16 * TP, (size_t)8 * ECAP);
+  const size_t union_bytes = max((size_t)8 * TP, (size_t)8 * ECAP);
+  float* s1 = reinterpret_cast<float*>(smem + union_bytes);
   Lists S;
   S.T = T;
   S.band = keys;
-  S.s1 = reinterpret_cast<float*>(smem + union_bytes);
-  S.s2 = S.s1 + T;
-  S.p1 = reinterpret_cast<int*>(S.s2 + T);
-  S.p2 = S.p1 + T;
+  S.s1 = s1;
+  S.s2 = s1 + T;
+  S.p2 = reinterpret_cast<int*>(S.s2 + T);
   S.vlo = S.p2 + T;
   S.vhi = S.vlo + T;
   S.rowpref = S.vhi + T;
@@ -159,67 +159,68 @@ __global__ void __launch_bounds__(NT) traverse_kernel(TraverseArgs a) {
     const int64_t L = a.L ? (int64_t)a.L[q] : (int64_t)a.L_scalar;
     const float* d1 = a.d1 + q * T;
     const float* d2 = a.d2 + q * T;
-    // 1. sort both coarse lists by (distance, index)
+    // 1. rows as they are, columns sorted by (distance, index)
     __syncthreads();
     for (int t = threadIdx.x; t < TP; t += NT) {
-      keys[t] = t < T ? ((uint64_t)f2ord(d1[t]) << 32) | (uint32_t)t : ~0ull;
-      keys[TP + t] = t < T ? ((uint64_t)f2ord(d2[t]) << 32) | (uint32_t)t : ~0ull;
+      keys[t] = t < T ? ((uint64_t)f2ord(d2[t]) << 32) | (uint32_t)t : ~0ull;
+      if (t < T) {
+        s1[t] = d1[t];
+        S.vlo[t] = 0;
+      }
     }
     block_bitonic_sort(keys, TP);
-    block_bitonic_sort(keys + TP, TP);
+    float s1max = -__int_as_float(0x7f800000);
     for (int t = threadIdx.x; t < T; t += NT) {
-      uint64_t k1 = keys[t], k2 = keys[TP + t];
-      S.s1[t] = ord2f((uint32_t)(k1 >> 32));
-      S.p1[t] = (int)(uint32_t)k1;
+      uint64_t k2 = keys[t];
       S.s2[t] = ord2f((uint32_t)(k2 >> 32));
       S.p2[t] = (int)(uint32_t)k2;
-      S.vlo[t] = 0;
+      s1max = fmaxf(s1max, s1[t]);
     }
-    __syncthreads();
-
-    const uint32_t max_ord = f2ord(__fadd_rn(S.s1[T - 1], S.s2[T - 1]));
-    long long base = 0;       // cells (all) with key <= tau_lo
+    // largest key: the largest row distance plus the largest column distance
+    const uint32_t s1max_ord = 0xffffffffu - block_min_u32(0xffffffffu - f2ord(s1max), red);
+    const uint32_t max_ord = f2ord(__fadd_rn(ord2f(s1max_ord), S.s2[T - 1]));
     long long committed = 0;  // points of the emitted cells
     int nout = 0;
     bool overflow = false;
-    int target = (int)fminf((float)ECAP, fmaxf(32.f, ceilf(2.f * (float)L / fmaxf(rho, 1.f))));
+    int target = (int)fminf((float)ECAP, fmaxf(32.f, ceilf((float)L / fmaxf(rho, 1.f))));
     bool done = false;
     while (!done) {
       // 2. the band's upper key: smallest frontier key first, then bisection
       uint32_t fr = 0xffffffffu;
       for (int u = threadIdx.x; u < T; u += NT) {
         int v = S.vlo[u];
-        if (v < T) fr = min(fr, f2ord(__fadd_rn(S.s1[u], S.s2[v])));
-        if (v == 0) break;  // later rows start at column 0 with larger s1
+        if (v < T) fr = min(fr, f2ord(__fadd_rn(s1[u], S.s2[v])));
       }
       const uint32_t hmin = block_min_u32(fr, red);
       if (hmin == 0xffffffffu) break;  // every cell visited
       uint32_t h;
-      long long cmin = count_cells(S, hmin, red) - base;
+      long long cmin = count_band(S, hmin, red);
       if (cmin > target) {
         if (cmin > ECAP) {  // one tie group larger than the band
           overflow = true;
           break;
         }
         h = hmin;
-      } else if (count_cells(S, max_ord, red) - base <= target) {
+      } else if (count_band(S, max_ord, red) <= target) {
         h = max_ord;
       } else {
         uint32_t lo = hmin, hi = max_ord;  // count(lo) <= target < count(hi)
         while (hi - lo > 1) {
           uint32_t mid = lo + ((hi - lo) >> 1);
-          if (count_cells(S, mid, red) - base <= target)
+          const long long c = count_band(S, mid, red);
+          if (c <= target) {
             lo = mid;
-          else
+            if (2 * c >= target) break;  // band large enough
+          } else {
             hi = mid;
+          }
         }
         h = lo;
       }
       // 3. enumerate the band: rows u, columns [vlo[u], vhi[u])
       for (int u = threadIdx.x; u < T; u += NT) {
-        int vl = S.vlo[u];
-        int vh = (f2ord(__fadd_rn(S.s1[u], S.s2[0])) > h) ? vl : row_count(S, u, vl, h);
-        S.vhi[u] = vh;
+        const int vl = S.vlo[u];
+        S.vhi[u] = (vl < T && f2ord(__fadd_rn(s1[u], S.s2[vl])) <= h) ? row_count(S, u, vl + 1, h) : vl;
       }
       __syncthreads();
       {  // exclusive prefix of the band lengths over rows
@@ -253,11 +254,11 @@ __global__ void __launch_bounds__(NT) traverse_kernel(TraverseArgs a) {
         }
         const int u = lo;
         const int v = S.vlo[u] + (e - S.rowpref[u]);
-        const uint32_t cell = (uint32_t)S.p1[u] * (uint32_t)T + (uint32_t)S.p2[v];
+        const uint32_t cell = (uint32_t)u * (uint32_t)T + (uint32_t)S.p2[v];
         const uint32_t b = a.offsets[cell];
         const uint32_t n = a.offsets[cell + 1] - b;
         if (n > 0) {
-          const float key = __fadd_rn(S.s1[u], S.s2[v]);
+          const float key = __fadd_rn(s1[u], S.s2[v]);
           int pos = atomicAdd(&nband_s, 1);
           S.band[pos] = ((uint64_t)f2ord(key) << 32) | cell;
           pts += n;
@@ -316,9 +317,8 @@ __global__ void __launch_bounds__(NT) traverse_kernel(TraverseArgs a) {
       nout += emit;
       committed += emit_pts;
       // next band
-      base += E;
       for (int u = threadIdx.x; u < T; u += NT) S.vlo[u] = S.vhi[u];
-      target = ECAP;
+      target = min(ECAP, 2 * target);
       __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -336,7 +336,7 @@ int traverse_band_capacity() { return ECAP; }
 static size_t traverse_smem(int T) {
   int TP = 1;
   while (TP < T) TP <<= 1;
-  return std::max((size_t)16 * TP, (size_t)8 * ECAP) + (size_t)T * 6 * 4 + (size_t)(T + 1) * 4;
+  return std::max((size_t)8 * TP, (size_t)8 * ECAP) + (size_t)T * 5 * 4 + (size_t)(T + 1) * 4;
 }
 
 void launch_traverse(const TraverseArgs& a, cudaStream_t st) {

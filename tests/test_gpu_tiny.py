@@ -63,6 +63,23 @@ def test_fbpq_tables_bit_exact(gpu, tiny_oracle):
     assert np.array_equal(a["X2"].cpu().numpy(), (2 * tab.X2).astype(np.float32))
 
 
+def test_point_cross_terms_bit_exact(gpu, tiny_oracle):
+    """The per-point Eq. 9 cross term 2<[c^1_i; c^2_j], r> used by the FBPQ scan."""
+    idx = tiny_oracle["index"]
+    cb, lists, tab = idx.cb, idx.lists, idx.tables
+    cell = np.repeat(np.arange(cb.T * cb.T), lists.counts())
+    i, j = cell // cb.T, cell % cb.T
+    m2 = cb.M // 2
+    codes = lists.codes.astype(np.int64)
+    ref = sum(tab.X1[i, k, codes[:, k]] for k in range(m2)) + sum(tab.X2[j, k, codes[:, m2 + k]] for k in range(m2))
+    got = gpu["ix"].arrays()["cross"].cpu().numpy()
+    assert np.array_equal(got, (2 * ref).astype(np.float32))
+    # and it is the explicit 2<c_ij, r> of the reconstruction (Eq. 7)
+    xr = O.reconstruct(cb, cell[:5000], lists.codes[:5000])
+    cen = np.concatenate([cb.C1[i[:5000]], cb.C2[j[:5000]]], axis=1)
+    assert np.array_equal(got[:5000].astype(np.float64), 2 * ((xr - cen) * cen).sum(1))
+
+
 def test_query_tables_bit_exact(gpu, tiny_oracle):
     cb = tiny_oracle["cb"]
     d1, d2, lut = gpu["ix"].query_tables(gpu["q"])
@@ -107,7 +124,7 @@ def test_traversal_uneven_budgets(gpu, tiny_oracle):
         assert np.array_equal(got[n][0], oc[lists.counts()[oc] > 0]) and npoints.cpu().numpy()[n] == total
 
 
-@pytest.mark.parametrize("scorer", ["fbpq", "recon"])
+@pytest.mark.parametrize("scorer", ["fbpq", "fbpq_tables", "recon"])
 def test_search_matches_oracle(gpu, tiny_oracle, scorer):
     w = tiny_oracle["w"]
     ids, dists = gpu["ix"].search(gpu["q"], w.L[0], w.k, scorer)
@@ -122,8 +139,9 @@ def test_search_matches_oracle(gpu, tiny_oracle, scorer):
 
 def test_fbpq_equals_reconstruction_on_gpu(gpu):
     a = [t.cpu().numpy() for t in gpu["ix"].search(gpu["q"], 20_000, 100, "fbpq")]
-    b = [t.cpu().numpy() for t in gpu["ix"].search(gpu["q"], 20_000, 100, "recon")]
-    assert np.array_equal(a[0], b[0]) and close(a[1], b[1]).all()
+    for other in ("fbpq_tables", "recon"):
+        b = [t.cpu().numpy() for t in gpu["ix"].search(gpu["q"], 20_000, 100, other)]
+        assert np.array_equal(a[0], b[0]) and close(a[1], b[1]).all()
 
 
 @pytest.mark.parametrize("k", [1, 7, 128, 300, 1024])
