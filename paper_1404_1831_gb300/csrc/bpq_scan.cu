@@ -432,10 +432,9 @@ void run_recon(const ScanArgs& a, cudaStream_t st) {
 
 template <int M, int SUB, int KP>
 void dispatch_scorer(const ScanArgs& a, int scorer, cudaStream_t st) {
-  if (scorer == BPQ_SCORER_FBPQ) {
-    BPQ_CHECK(a.cross || a.nq == 0, BPQ_ESTATE, "FBPQ needs the per-point cross terms (global variant)");
+  if (scorer == BPQ_SCORER_FBPQ)
     run_fbpq<M, KP, true>(a, st);
-  } else if (scorer == BPQ_SCORER_FBPQ_TABLES)
+  else if (scorer == BPQ_SCORER_FBPQ_TABLES)
     run_fbpq<M, KP, false>(a, st);
   else if (scorer == BPQ_SCORER_RECON)
     run_recon<M, SUB, KP, false>(a, st);
