@@ -158,17 +158,139 @@ __device__ int block_excl_scan(int x, int* tmp, int* total) {
 }
 
 // ---------------------------------------------------------------------------
+// Block-wide top-k: accepted composites go to a shared buffer; when it fills up,
+// a radix select on the distance bits finds the k-th smallest distance v_k of
+// the buffer, everything above it is dropped and v_k becomes the threshold.
+// The buffer therefore always holds every candidate that can still be in the
+// top k (ties at v_k included); the final list is its exact (distance, id) sort.
+// ---------------------------------------------------------------------------
+template <int NT>
+struct BlockTopK {
+  static constexpr int CAP = 2048;  // buffer entries; rounds add at most NT * ILP
+  uint64_t* buf;    // CAP
+  uint64_t* alt;    // CAP (compaction target)
+  int* nbuf;        // shared counter
+  unsigned long long* thr;  // shared threshold composite
+  uint32_t* hist;   // 256 + 8 scratch
+};
+
+// k-th smallest value of the distance bits (high 32) among buf[0..n): 4 passes of
+// 8-bit histograms.  All threads call; returns the value on every thread.
+template <int NT>
+__device__ uint32_t select_kth_hi(const uint64_t* buf, int n, int k, uint32_t* hist) {
+  uint32_t prefix = 0, mask = 0;
+  int rank = k;  // 1-based rank still to find among keys matching prefix
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int t = threadIdx.x; t < 256; t += NT) hist[t] = 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += NT) {
+      const uint32_t key = (uint32_t)(buf[e] >> 32);
+      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int l = threadIdx.x;
+      uint32_t c[8], tot = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        c[i] = hist[l * 8 + i];
+        tot += c[i];
+      }
+      uint32_t incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (l >= o) incl += y;
+      }
+      uint32_t run = incl - tot;
+      // the bin where the running count reaches `rank`
+      const bool mine = run < (uint32_t)rank && (uint32_t)rank <= incl;
+      if (mine) {
+        int d = 0;
+        while (run + c[d] < (uint32_t)rank) run += c[d++];
+        hist[256] = (uint32_t)(l * 8 + d);
+        hist[257] = run;
+      }
+    }
+    __syncthreads();
+    const uint32_t d = hist[256];
+    rank -= (int)hist[257];
+    prefix |= d << shift;
+    mask |= 255u << shift;
+    __syncthreads();
+  }
+  return prefix;
+}
+
+// Keep the entries whose distance bits are <= v (the k-th smallest): moves them
+// to alt, swaps buffers.  Updates *nbuf and the threshold.
+template <int NT>
+__device__ void block_topk_prune(BlockTopK<NT>& tk, int k) {
+  const int n = *tk.nbuf;
+  if (n <= k) {
+    __syncthreads();
+    return;
+  }
+  const uint32_t v = select_kth_hi<NT>(tk.buf, n, k, tk.hist);
+  if (threadIdx.x == 0) tk.hist[258] = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += NT) {
+    const uint64_t x = tk.buf[e];
+    if ((uint32_t)(x >> 32) <= v) tk.alt[atomicAdd(&tk.hist[258], 1u)] = x;
+  }
+  __syncthreads();
+  const int kept = (int)tk.hist[258];
+  uint64_t* t = tk.buf;
+  tk.buf = tk.alt;
+  tk.alt = t;
+  if (kept > BlockTopK<NT>::CAP / 2) {
+    // a huge tie group at v: sort exactly and keep k
+    int n2 = 1;
+    while (n2 < kept) n2 <<= 1;
+    for (int e = kept + threadIdx.x; e < n2; e += NT) tk.buf[e] = EMPTY;
+    block_bitonic_sort(tk.buf, n2);
+    if (threadIdx.x == 0) {
+      *tk.nbuf = k;
+      *tk.thr = tk.buf[k - 1];
+    }
+  } else if (threadIdx.x == 0) {
+    *tk.nbuf = kept;
+    *tk.thr = ((unsigned long long)v << 32) | 0xffffffffull;
+  }
+  __syncthreads();
+}
+
+// Final: exact (distance, id) order of the buffer, first k written out.
+template <int NT>
+__device__ void block_topk_finish(BlockTopK<NT>& tk, int k, int32_t* out_ids, float* out_dists) {
+  block_topk_prune<NT>(tk, k);
+  const int n = *tk.nbuf;
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  for (int e = n + threadIdx.x; e < n2; e += NT) tk.buf[e] = EMPTY;
+  block_bitonic_sort(tk.buf, n2);
+  for (int r = threadIdx.x; r < k; r += NT) {
+    const uint64_t x = r < n ? tk.buf[r] : EMPTY;
+    out_ids[r] = (x == EMPTY) ? -1 : (int32_t)(uint32_t)x;
+    out_dists[r] = (x == EMPTY) ? __int_as_float(0x7f800000) : ord2f((uint32_t)(x >> 32));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FBPQ scan: one CTA per query.
 //  POINT = true : per-point cross term (one coalesced float per candidate)
 //  POINT = false: cross terms gathered from the X1 / X2 tables (2M lookups)
 // ---------------------------------------------------------------------------
-template <int M, int KP, bool POINT>
+template <int M, bool POINT>
 __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
   constexpr int NT = 256, NW = NT / 32, CH = NT, ILP = 4, M2 = M / 2;
-  using TK = WarpTopK<KP>;
+  constexpr int SUB = 4096;          // candidates per cell-map refresh
+  constexpr int PER = SUB / NT;      // candidates per thread in the map
+  using TK = BlockTopK<NT>;
   extern __shared__ __align__(16) unsigned char smem[];
   float* lut = reinterpret_cast<float*>(smem);
-  uint64_t* areas = reinterpret_cast<uint64_t*>(lut + M * KSUB);
+  uint64_t* bufs = reinterpret_cast<uint64_t*>(lut + M * KSUB);  // 2 x CAP
+  uint8_t* cmap = reinterpret_cast<uint8_t*>(bufs + 2 * TK::CAP);  // SUB
   __shared__ uint32_t c_beg[CH];
   __shared__ uint32_t c_x1[CH];
   __shared__ uint32_t c_x2[CH];
@@ -176,6 +298,8 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
   __shared__ int c_pref[CH + 1];
   __shared__ int scan_tmp[NW + 1];
   __shared__ unsigned long long thr;
+  __shared__ int nbuf;
+  __shared__ uint32_t hist[260];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = a.k;
 
@@ -185,9 +309,11 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
       const float4* src = reinterpret_cast<const float4*>(a.lut + q * M * KSUB);
       for (int t = threadIdx.x; t < M * KSUB / 4; t += NT) reinterpret_cast<float4*>(lut)[t] = src[t];
     }
-    TK tk;
-    tk.init(areas + warp * TK::AREA);
-    if (threadIdx.x == 0) thr = EMPTY;
+    TK tk{bufs, bufs + TK::CAP, &nbuf, &thr, hist};
+    if (threadIdx.x == 0) {
+      thr = EMPTY;
+      nbuf = 0;
+    }
     const int nc = max(0, a.ncells[q]);
     const bpq_cell* cl = a.cells + q * (int64_t)a.cap;
     for (int cs = 0; cs < nc; cs += CH) {
@@ -207,74 +333,87 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
       int total;
       int ex = block_excl_scan<NT>(cnt, scan_tmp, &total);
       if ((int)threadIdx.x < nch) c_pref[threadIdx.x] = ex;
+      if (threadIdx.x == 0) c_pref[nch] = total;
       __syncthreads();
       const int P = total;
-      for (int base = 0; base < P; base += NT * ILP) {
-        Code<M> code[ILP];
-        float pc[ILP];
-        int cidx[ILP];
-        uint32_t pos[ILP];
+      for (int sub = 0; sub < P; sub += SUB) {
+        // cell of every candidate of this slice: one search, then a walk
+        {
+          const int f0 = sub + threadIdx.x * PER;
+          if (f0 < P) {
+            int c = find_cell(c_pref, nch, f0);
+            const int fe = min(P, f0 + PER);
+            for (int f = f0; f < fe; ++f) {
+              while (c_pref[c + 1] <= f) ++c;
+              cmap[f - sub] = (uint8_t)c;
+            }
+          }
+        }
+        __syncthreads();
+        const int Pe = min(P, sub + SUB);
+        for (int base = sub; base < Pe; base += NT * ILP) {
+          Code<M> code[ILP];
+          float pc[ILP];
+          int cidx[ILP];
+          uint32_t pos[ILP];
 #pragma unroll
-        for (int u = 0; u < ILP; ++u) {
-          // the lanes of a warp hold 32 consecutive candidates: one search for the
-          // warp's first candidate, then a search in the next 32 cells at most
-          const int fw = base + u * NT + warp * 32;
-          const int f = fw + lane;
-          cidx[u] = -1;
-          if (fw < P) {
-            const int c0 = find_cell(c_pref, nch, fw);
-            if (f < P) {
-              int lo = c0, hi = min(nch, c0 + 32);
-              while (hi - lo > 1) {
-                int mid = (lo + hi) >> 1;
-                if (c_pref[mid] <= f) lo = mid; else hi = mid;
-              }
-              cidx[u] = lo;
-              pos[u] = c_beg[lo] + (uint32_t)(f - c_pref[lo]);
+          for (int u = 0; u < ILP; ++u) {
+            const int f = base + u * NT + threadIdx.x;
+            cidx[u] = -1;
+            if (f < Pe) {
+              const int c = cmap[f - sub];
+              cidx[u] = c;
+              pos[u] = c_beg[c] + (uint32_t)(f - c_pref[c]);
               code[u].load(a.codes, pos[u]);
               if (POINT) pc[u] = __ldg(a.cross + pos[u]);
             }
           }
-        }
-        const unsigned long long th = *(volatile unsigned long long*)&thr;
-        const uint32_t th_hi = (uint32_t)(th >> 32);
+          const unsigned long long th = *(volatile unsigned long long*)&thr;
+          const uint32_t th_hi = (uint32_t)(th >> 32);
 #pragma unroll
-        for (int u = 0; u < ILP; ++u) {
-          bool acc = false;
-          uint64_t comp = 0;
-          if (cidx[u] >= 0) {
-            const int c = cidx[u];
-            float part;
-            if (POINT) {
-              part = pc[u];
+          for (int u = 0; u < ILP; ++u) {
+            bool acc = false;
+            uint64_t comp = 0;
+            if (cidx[u] >= 0) {
+              const int c = cidx[u];
+              float part;
+              if (POINT) {
+                part = pc[u];
 #pragma unroll
-              for (int kk = 0; kk < M; ++kk) part += lut[kk * KSUB + code[u].byte(kk)];
-            } else {
-              part = 0.f;
-              const float* x1 = a.X1 + c_x1[c];
-              const float* x2 = a.X2 + c_x2[c];
+                for (int kk = 0; kk < M; ++kk) part += lut[kk * KSUB + code[u].byte(kk)];
+              } else {
+                part = 0.f;
+                const float* x1 = a.X1 + c_x1[c];
+                const float* x2 = a.X2 + c_x2[c];
 #pragma unroll
-              for (int kk = 0; kk < M; ++kk) {
-                const uint32_t b = code[u].byte(kk);
-                const float xv = (kk < M2) ? __ldg(x1 + kk * KSUB + b) : __ldg(x2 + (kk - M2) * KSUB + b);
-                part += lut[kk * KSUB + b] + xv;
+                for (int kk = 0; kk < M; ++kk) {
+                  const uint32_t b = code[u].byte(kk);
+                  const float xv = (kk < M2) ? __ldg(x1 + kk * KSUB + b) : __ldg(x2 + (kk - M2) * KSUB + b);
+                  part += lut[kk * KSUB + b] + xv;
+                }
+              }
+              const float dist = c_key[c] + part;
+              const uint32_t o = f2ord(dist);
+              if (o <= th_hi) {
+                comp = ((uint64_t)o << 32) | (uint32_t)__ldg(a.ids + pos[u]);
+                acc = comp <= th;
               }
             }
-            const float dist = c_key[c] + part;
-            const uint32_t o = f2ord(dist);
-            if (o <= th_hi) {
-              comp = ((uint64_t)o << 32) | (uint32_t)__ldg(a.ids + pos[u]);
-              acc = comp < th;
+            const unsigned m = __ballot_sync(0xffffffffu, acc);
+            if (m) {
+              int at = 0;
+              if (lane == 0) at = atomicAdd(&nbuf, __popc(m));
+              at = __shfl_sync(0xffffffffu, at, 0);
+              if (acc) tk.buf[at + __popc(m & lanemask_lt())] = comp;
             }
           }
-          tk.offer(acc, comp, k, &thr);
+          __syncthreads();
+          if (nbuf > TK::CAP - NT * ILP) block_topk_prune<NT>(tk, k);
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
-    if (tk.nbuf > 0) tk.flush(k, &thr);
-    __syncthreads();
-    merge_lists(areas, NW, KP, TK::AREA, k, a.out_ids + q * k, a.out_dists + q * k);
+    block_topk_finish<NT>(tk, k, a.out_ids + q * k, a.out_dists + q * k);
   }
 }
 
@@ -404,11 +543,10 @@ __global__ void __launch_bounds__(NW * 32) recon_scan_kernel(ScanArgs a) {
   }
 }
 
-template <int M, int KP, bool POINT>
+template <int M, bool POINT>
 void run_fbpq(const ScanArgs& a, cudaStream_t st) {
-  using TK = WarpTopK<KP>;
-  const size_t smem = (size_t)M * KSUB * 4 + (size_t)8 * TK::AREA * 8;
-  auto kern = fbpq_scan_kernel<M, KP, POINT>;
+  const size_t smem = (size_t)M * KSUB * 4 + (size_t)2 * BlockTopK<256>::CAP * 8 + 4096;
+  auto kern = fbpq_scan_kernel<M, POINT>;
   BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
   kern<<<grid, 256, smem, st>>>(a);
@@ -433,9 +571,9 @@ void run_recon(const ScanArgs& a, cudaStream_t st) {
 template <int M, int SUB, int KP>
 void dispatch_scorer(const ScanArgs& a, int scorer, cudaStream_t st) {
   if (scorer == BPQ_SCORER_FBPQ)
-    run_fbpq<M, KP, true>(a, st);
+    run_fbpq<M, true>(a, st);
   else if (scorer == BPQ_SCORER_FBPQ_TABLES)
-    run_fbpq<M, KP, false>(a, st);
+    run_fbpq<M, false>(a, st);
   else if (scorer == BPQ_SCORER_RECON)
     run_recon<M, SUB, KP, false>(a, st);
   else
