@@ -187,7 +187,8 @@ size_t bpq_search_workspace_size(const bpq_index* idx, int64_t nq, int64_t L_max
 
 /*
  * bpq_traverse — visit order of the inverted multi-index (§2.3.3): for each query,
- * the non-empty cells in non-decreasing d1[i] + d2[j] order, ties by cell id,
+ * the non-empty cells in non-decreasing d1[i] + d2[j] order, ties by cell id
+ * (bpq_search visits the same cells but does not need them in order),
  * up to and including the first cell at which the visited points reach L (the
  * multi-sequence stopping rule; all cells if the index holds fewer points).
  * Empty cells consume order but hold no candidates, so they are not listed.

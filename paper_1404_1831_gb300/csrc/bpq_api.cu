@@ -241,6 +241,7 @@ void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t*
     }
     ta.T = ix.p.T;
     ta.rho = rho;
+    ta.ordered = scan ? 0 : 1;
     ta.status = reinterpret_cast<int32_t*>(w + l.status);
     ta.nq = nc;
     if (scan) {

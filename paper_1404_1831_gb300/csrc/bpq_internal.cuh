@@ -186,6 +186,7 @@ struct TraverseArgs {
   int32_t T;
   int32_t cap;       // output cells per query
   float rho;         // mean points per non-empty cell (sizes the first band)
+  int32_t ordered;   // 1: emit each band sorted by (key, cell id); 0: any order
   bpq_cell* cells;   // nq x cap
   int32_t* ncells;
   int64_t* npoints;
