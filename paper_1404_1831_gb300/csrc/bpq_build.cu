@@ -249,7 +249,7 @@ __global__ void radix_scatter_kernel(const uint64_t* kin, const uint32_t* vin, u
   constexpr int NW = NTB / 32;
   __shared__ uint32_t run[256];
   __shared__ uint32_t wc[NW][256];
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
   run[threadIdx.x] = goff[(int64_t)threadIdx.x * ntiles + blockIdx.x];
   const int64_t t0 = (int64_t)blockIdx.x * RTILE;
   for (int r = 0; r < 16; ++r) {

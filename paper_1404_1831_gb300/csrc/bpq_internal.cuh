@@ -104,6 +104,23 @@ __device__ __forceinline__ void warp_bitonic_sort(uint64_t* a, int n) {
   __syncwarp();
 }
 
+// Histogram increment aggregated over the lanes of a warp that hit the same bin
+// (one shared-memory atomic per distinct bin instead of one per lane).  Every
+// lane of the warp must call it; lanes with valid == false add nothing.
+__device__ __forceinline__ void warp_hist_add(uint32_t* hist, uint32_t bin, bool valid) {
+  const uint32_t peers = __match_any_sync(0xffffffffu, valid ? bin : 0xffffffffu);
+  if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+}
+
+// Weighted version: adds w (< 2^32) of every lane to its bin, 64-bit totals.
+__device__ __forceinline__ void warp_hist_add_w(unsigned long long* hist, uint32_t bin, uint32_t w, bool valid) {
+  const uint32_t peers = __match_any_sync(0xffffffffu, valid ? bin : 0xffffffffu);
+  const uint32_t ww = valid ? w : 0u;
+  const uint32_t lo = __reduce_add_sync(peers, ww & 0xffffu);
+  const uint32_t hi = __reduce_add_sync(peers, ww >> 16);
+  if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&hist[bin], (unsigned long long)lo + ((unsigned long long)hi << 16));
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -183,9 +183,10 @@ __device__ uint32_t select_kth_hi(const uint64_t* buf, int n, int k, uint32_t* h
   for (int shift = 24; shift >= 0; shift -= 8) {
     for (int t = threadIdx.x; t < 256; t += NT) hist[t] = 0;
     __syncthreads();
-    for (int e = threadIdx.x; e < n; e += NT) {
-      const uint32_t key = (uint32_t)(buf[e] >> 32);
-      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    for (int e0 = 0; e0 < n; e0 += NT) {
+      const int e = e0 + threadIdx.x;
+      const uint32_t key = e < n ? (uint32_t)(buf[e] >> 32) : 0u;
+      warp_hist_add(hist, (key >> shift) & 255u, e < n && (key & mask) == prefix);
     }
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
   __shared__ unsigned long long thr;
   __shared__ int nbuf;
   __shared__ uint32_t hist[260];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   const int k = a.k;
 
   for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {

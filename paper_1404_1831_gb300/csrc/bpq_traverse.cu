@@ -108,15 +108,22 @@ __device__ long long block_incl_scan(long long x, Red& r, long long* total) {
 // Stable LSD radix sort (ascending) of n uint32 keys with uint16 payloads, 8-bit
 // digits.  Elements are ranked in rounds of NT (element r*NT + t by thread t):
 // inside a round equal digits keep thread order (warp match plus per-warp
-// counts) and rounds run in order, so every pass is stable.  Four passes (an
-// even number of buffer swaps) leave the result in k, v.
-__device__ void block_radix_sort(uint32_t* k, uint16_t* v, uint32_t* k2, uint16_t* v2, int n, uint32_t* run,
-                                 uint32_t* wc) {
+// counts) and rounds run in order, so every pass is stable.  A pass whose digit
+// every key shares (kmin and kmax agree on all bits from it up) is skipped.  The
+// result ends in k, v.
+__device__ void block_radix_sort(uint32_t* k, uint16_t* v, uint32_t* k2, uint16_t* v2, int n, uint32_t kmin,
+                                 uint32_t kmax, uint32_t* run, uint32_t* wc) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  uint32_t* const k0 = k;
+  uint16_t* const v0 = v;
   for (int shift = 0; shift < 32; shift += 8) {
+    if (((kmin ^ kmax) >> shift) == 0) break;  // this digit and all above are common
     run[threadIdx.x] = 0;
     __syncthreads();
-    for (int e = threadIdx.x; e < n; e += NT) atomicAdd(&run[(k[e] >> shift) & 255u], 1u);
+    for (int e0 = 0; e0 < n; e0 += NT) {
+      const int e = e0 + threadIdx.x;
+      warp_hist_add(run, e < n ? (k[e] >> shift) & 255u : 0u, e < n);
+    }
     __syncthreads();
     if (w == 0) {  // exclusive scan of the 256 digit counts
       uint32_t c[8], tot = 0;
@@ -171,6 +178,13 @@ __device__ void block_radix_sort(uint32_t* k, uint16_t* v, uint32_t* k2, uint16_
     v = v2;
     v2 = tv;
   }
+  if (k != k0) {  // odd number of passes: copy back
+    for (int e = threadIdx.x; e < n; e += NT) {
+      k0[e] = k[e];
+      v0[e] = v[e];
+    }
+  }
+  __syncthreads();
 }
 
 struct Lists {
@@ -207,6 +221,41 @@ __device__ long long count_band(const Lists& S, uint32_t h, Red& r) {
   return block_sum(c, r);
 }
 
+constexpr int NTH = 8;  // thresholds evaluated per block reduction
+
+// Band cell counts for NTH ascending thresholds h[0..NTH) at once; the results
+// land in out[0..NTH) on every thread.
+__device__ void count_band_multi(const Lists& S, const uint32_t* h, long long* out, long long (*red8)[NTH]) {
+  long long c[NTH];
+#pragma unroll
+  for (int j = 0; j < NTH; ++j) c[j] = 0;
+  for (int u = threadIdx.x; u < S.T; u += NT) {
+    const int v = S.vlo[u];
+    if (v >= S.T) continue;
+    const uint32_t kf = f2ord(__fadd_rn(S.s1[u], S.s2[v]));
+    if (kf > h[NTH - 1]) continue;
+#pragma unroll
+    for (int j = 0; j < NTH; ++j)
+      if (kf <= h[j]) c[j] += row_count(S, u, v + 1, h[j]) - v;
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < NTH; ++j) c[j] = warp_sum(c[j]);
+  __syncthreads();
+  if (l == 0)
+#pragma unroll
+    for (int j = 0; j < NTH; ++j) red8[w][j] = c[j];
+  __syncthreads();
+  if (threadIdx.x < NTH) {
+    long long t = 0;
+    for (int x = 0; x < NW; ++x) t += red8[x][threadIdx.x];
+    red8[NW][threadIdx.x] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NTH; ++j) out[j] = red8[NW][j];
+}
+
 // Smallest key v (as ord bits) among the band entries such that the points of
 // the entries with key <= v reach `need`; *below receives the points of the
 // entries with key < v.  Weighted 8-bit radix select.
@@ -218,9 +267,10 @@ __device__ uint32_t weighted_select(const uint64_t* band, const uint32_t* cnt, i
   for (int shift = 24; shift >= 0; shift -= 8) {
     hist[threadIdx.x] = 0;
     __syncthreads();
-    for (int e = threadIdx.x; e < n; e += NT) {
-      const uint32_t key = (uint32_t)(band[e] >> 32);
-      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], (unsigned long long)cnt[e]);
+    for (int e0 = 0; e0 < n; e0 += NT) {
+      const int e = e0 + threadIdx.x;
+      const uint32_t key = e < n ? (uint32_t)(band[e] >> 32) : 0u;
+      warp_hist_add_w(hist, (key >> shift) & 255u, e < n ? cnt[e] : 0u, e < n && (key & mask) == prefix);
     }
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -262,6 +312,7 @@ __global__ void __launch_bounds__(NT) traverse_kernel(TraverseArgs a) {
   __shared__ int nout_s;
   __shared__ long long emit_pts_s;
   __shared__ unsigned long long hist[258];
+  __shared__ long long red8[NW + 1][NTH];
   const float rho = a.rho;
   const int T = a.T;
   int TP = 1;
@@ -297,8 +348,12 @@ __global__ void __launch_bounds__(NT) traverse_kernel(TraverseArgs a) {
     __syncthreads();
     float s1min = __int_as_float(0x7f800000), s1max = -__int_as_float(0x7f800000);
     int argmin = 0;
+    uint32_t kmin = 0xffffffffu, kmax = 0u;
     for (int t = threadIdx.x; t < T; t += NT) {
-      sk[t] = f2ord(d2[t]);
+      const uint32_t kk = f2ord(d2[t]);
+      sk[t] = kk;
+      kmin = min(kmin, kk);
+      kmax = max(kmax, kk);
       sv[t] = (uint16_t)t;
       const float x = d1[t];
       s1[t] = x;
@@ -309,8 +364,9 @@ __global__ void __launch_bounds__(NT) traverse_kernel(TraverseArgs a) {
       }
       s1max = fmaxf(s1max, x);
     }
-    __syncthreads();
-    block_radix_sort(sk, sv, sk2, sv2, T, srun, swc);
+    kmin = block_min_u32(kmin, red);
+    kmax = 0xffffffffu - block_min_u32(0xffffffffu - kmax, red);
+    block_radix_sort(sk, sv, sk2, sv2, T, kmin, kmax, srun, swc);
     for (int t = threadIdx.x; t < T; t += NT) {
       s2[t] = ord2f(sk[t]);
       p2[t] = sv[t];
@@ -367,28 +423,42 @@ __global__ void __launch_bounds__(NT) traverse_kernel(TraverseArgs a) {
             clo = chi;
           }
         }
-        int it = 0;
+        // each round evaluates NTH thresholds spread around the interpolated one
+        // (counts grow like the square of the key inside a staircase)
         while (hi - lo > 1 && 2 * clo < target) {
-          uint32_t mid;
-          if (it < 6) {  // interpolate on sqrt(count), inside the bracket
-            const float flo = ord2f(lo), fhi = ord2f(hi);
-            const float sl = sqrtf((float)clo), sh = sqrtf((float)chi), sa = sqrtf(0.75f * (float)target);
-            float frac = (sa - sl) / fmaxf(sh - sl, 1e-6f);
-            frac = fminf(fmaxf(frac, 0.02f), 0.98f);
-            mid = f2ord(flo + frac * (fhi - flo));
-            if (mid <= lo) mid = lo + 1;
-            if (mid >= hi) mid = hi - 1;
-          } else {
-            mid = lo + ((hi - lo) >> 1);
+          const float flo = ord2f(lo), fhi = ord2f(hi);
+          const float sl = sqrtf((float)clo), sh = sqrtf((float)chi), sa = sqrtf(0.75f * (float)target);
+          const float est = fminf(fmaxf((sa - sl) / fmaxf(sh - sl, 1e-6f), 0.02f), 0.98f);
+          const float spread[NTH] = {0.35f, 0.55f, 0.75f, 0.9f, 1.0f, 1.12f, 1.3f, 1.6f};
+          uint32_t th[NTH];
+          uint32_t prev = lo;
+#pragma unroll
+          for (int j = 0; j < NTH; ++j) {
+            uint32_t t = f2ord(flo + fminf(est * spread[j], 0.999f) * (fhi - flo));
+            if (t <= prev) t = prev + 1;
+            if (t >= hi) t = hi - 1;
+            th[j] = max(t, prev);
+            prev = th[j];
           }
-          ++it;
-          const long long c = count_band(S, mid, red);
-          if (c <= target) {
-            lo = mid;
-            clo = c;
-          } else {
-            hi = mid;
-            chi = c;
+          if (hi - lo <= (uint32_t)NTH + 1) {  // narrow bracket: every key in it
+#pragma unroll
+            for (int j = 0; j < NTH; ++j) th[j] = min(hi - 1, lo + 1 + j);
+          }
+          long long cnt[NTH];
+          count_band_multi(S, th, cnt, red8);
+          int best = -1;
+#pragma unroll
+          for (int j = 0; j < NTH; ++j)
+            if (cnt[j] <= target) best = j;
+          if (best >= 0) {
+            lo = th[best];
+            clo = cnt[best];
+          }
+          for (int j = NTH - 1; j > best; --j) {
+            if (th[j] > lo) {
+              hi = th[j];
+              chi = cnt[j];
+            }
           }
         }
         h = lo;
