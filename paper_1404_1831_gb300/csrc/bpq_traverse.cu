@@ -3,21 +3,20 @@
 // The paper walks cells in increasing d1[i] + d2[j] with the multi-sequence
 // algorithm (a priority queue over the two sorted coarse-distance lists) until
 // the visited cells hold l points.  A sequential heap is a poor fit for a GPU,
-// so this kernel (one CTA per query) computes the same visited set in bands:
+// so this kernel (one CTA per query) computes the same visited set in bands of
+// the (row i, sorted column v) grid, where row i's keys d1[i] + s2[v] rise with v:
 //
-//   1. sort d2 with its indices (stable radix sort): s2, p2.  Every row i then
-//      has keys d1[i] + s2[v] that are non-decreasing in v, and the cells of row
-//      i visited so far are the columns v < vlo[i] (rows need no order);
-//   2. a band is every cell with tau_lo < key <= tau_hi.  tau_hi is chosen so the
-//      band holds between half the target and the target number of cells: the
-//      cell count of a candidate tau is a binary search in each row whose next
-//      cell is <= tau, summed over the block, and tau is searched by
-//      interpolation on the square root of the count (the region is a
-//      two-dimensional staircase) inside a bracket.  The first band targets
-//      L / rho cells (rho = mean points per non-empty cell), later ones twice
-//      the previous target, up to a fixed capacity;
-//   3. the band's cells are enumerated row by row, their point counts read from
-//      the cell offsets and empty cells dropped;
+//   1. only the columns with the smallest d2 are sorted: a sample gives a value
+//      theta, the columns with d2 <= theta are compacted and sorted by one warp
+//      in registers (s2, p2).  Every cell outside this prefix has a key of at
+//      least min(d1) + theta ("the limit"), so bands stay below the limit; a
+//      query that needs more columns falls back to a full radix sort;
+//   2. a band is every cell with tau_lo < key <= tau_hi.  The rows whose next
+//      cell lies under an upper guess are compacted, and warp 0 alone picks
+//      tau_hi (interpolation on the square root of the cell count, the region
+//      being a staircase) so the band holds a bounded number of cells;
+//   3. the band's cells are enumerated over the compacted rows, their point
+//      counts read from the cell offsets and empty cells dropped;
 //   4. if the band's points do not reach the budget, every cell is emitted and
 //      the next band starts at tau_hi; otherwise the band is cut at the first
 //      cell, in (key, cell id) order, at which the running count reaches L.  The
@@ -41,6 +40,7 @@ namespace {
 constexpr int NT = 256;  // threads per CTA; also the radix of the sorts and selects
 constexpr int NW = NT / 32;
 constexpr int ECAP = 2048;  // band capacity (cells, empty ones included)
+constexpr uint32_t ORD_INF = 0xffffffffu;
 
 struct Red {
   long long v[33];
@@ -61,22 +61,28 @@ __device__ long long block_sum(long long x, Red& r) {
   return r.v[32];
 }
 
-__device__ uint32_t block_min_u32(uint32_t x, Red& r) {
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long x) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+  for (int o = 16; o > 0; o >>= 1) x = min(x, (unsigned long long)__shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+__device__ unsigned long long block_min_u64(unsigned long long x, Red& r) {
+  x = warp_min_u64(x);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
-  if (l == 0) r.v[w] = x;
+  if (l == 0) r.v[w] = (long long)x;
   __syncthreads();
   if (w == 0) {
-    uint32_t t = (l < NW) ? (uint32_t)r.v[l] : 0xffffffffu;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t = min(t, __shfl_xor_sync(0xffffffffu, t, o));
-    if (l == 0) r.v[32] = t;
+    unsigned long long t = (l < NW) ? (unsigned long long)r.v[l] : ~0ull;
+    t = warp_min_u64(t);
+    if (l == 0) r.v[32] = (long long)t;
   }
   __syncthreads();
-  return (uint32_t)r.v[32];
+  return (unsigned long long)r.v[32];
 }
+
+__device__ uint32_t block_min_u32(uint32_t x, Red& r) { return (uint32_t)block_min_u64(x, r); }
 
 // Inclusive scan of one value per thread; returns this thread's inclusive sum;
 // *total receives the block total.
@@ -105,19 +111,78 @@ __device__ long long block_incl_scan(long long x, Red& r, long long* total) {
   return x + off;
 }
 
+// Bitonic sort (ascending) of 32 * N keys held by one warp, N per lane, element
+// lane * N + i in x[i].  Pairs closer than N are in the same lane; farther
+// pairs are exchanged with shuffles.  Fully unrolled, so register indices are
+// compile-time constants.
+template <int N>
+__device__ __forceinline__ void warp_sort(uint64_t (&x)[N]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 32 * N; size <<= 1) {
+#pragma unroll
+    for (int j = size >> 1; j > 0; j >>= 1) {
+      if (j < N) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const int p = i ^ j;
+          if (p > i) {
+            const bool up = (((lane * N + i) & size) == 0);
+            const uint64_t a = x[i], b = x[p];
+            const bool sw = (a > b) == up;
+            x[i] = sw ? b : a;
+            x[p] = sw ? a : b;
+          }
+        }
+      } else {
+        const int lj = j / N;
+        const bool lower = (lane & lj) == 0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const uint64_t o = __shfl_xor_sync(0xffffffffu, x[i], lj);
+          const bool up = (((lane * N + i) & size) == 0);
+          x[i] = (lower == up) ? min(x[i], o) : max(x[i], o);
+        }
+      }
+    }
+  }
+}
+
+// Warp 0 sorts buf[0..n) (n <= 32 * N, padding with ~0) in place.
+template <int N>
+__device__ void warp_sort_buf_n(uint64_t* buf, int n) {
+  const int lane = threadIdx.x & 31;
+  uint64_t x[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int e = lane * N + i;
+    x[i] = e < n ? buf[e] : ~0ull;
+  }
+  warp_sort<N>(x);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int e = lane * N + i;
+    if (e < n) buf[e] = x[i];
+  }
+}
+
+// Warp 0 sorts buf[0..n), n <= 256.
+__device__ void warp_sort_buf(uint64_t* buf, int n) {
+  if (n <= 32) warp_sort_buf_n<1>(buf, n);
+  else if (n <= 64) warp_sort_buf_n<2>(buf, n);
+  else if (n <= 128) warp_sort_buf_n<4>(buf, n);
+  else warp_sort_buf_n<8>(buf, n);
+}
+
 // Stable LSD radix sort (ascending) of n uint32 keys with uint16 payloads, 8-bit
-// digits.  Elements are ranked in rounds of NT (element r*NT + t by thread t):
-// inside a round equal digits keep thread order (warp match plus per-warp
-// counts) and rounds run in order, so every pass is stable.  A pass whose digit
-// every key shares (kmin and kmax agree on all bits from it up) is skipped.  The
-// result ends in k, v.
-__device__ void block_radix_sort(uint32_t* k, uint16_t* v, uint32_t* k2, uint16_t* v2, int n, uint32_t kmin,
-                                 uint32_t kmax, uint32_t* run, uint32_t* wc) {
+// digits (the full-sort fallback).  Elements are ranked in rounds of NT: inside
+// a round equal digits keep thread order (warp match plus per-warp counts) and
+// rounds run in order, so every pass is stable.  Four passes leave the result in
+// k, v.
+__device__ void block_radix_sort(uint32_t* k, uint16_t* v, uint32_t* k2, uint16_t* v2, int n, uint32_t* run,
+                                 uint32_t* wc) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  uint32_t* const k0 = k;
-  uint16_t* const v0 = v;
   for (int shift = 0; shift < 32; shift += 8) {
-    if (((kmin ^ kmax) >> shift) == 0) break;  // this digit and all above are common
     run[threadIdx.x] = 0;
     __syncthreads();
     for (int e0 = 0; e0 < n; e0 += NT) {
@@ -178,82 +243,20 @@ __device__ void block_radix_sort(uint32_t* k, uint16_t* v, uint32_t* k2, uint16_
     v = v2;
     v2 = tv;
   }
-  if (k != k0) {  // odd number of passes: copy back
-    for (int e = threadIdx.x; e < n; e += NT) {
-      k0[e] = k[e];
-      v0[e] = v[e];
-    }
-  }
-  __syncthreads();
 }
 
-struct Lists {
-  const float* s1;     // d1 in row order (unsorted)
-  const float* s2;     // d2 sorted ascending
-  const uint16_t* p2;  // column of s2[v]
-  uint16_t* vlo;       // per row: columns already emitted (keys <= tau_lo)
-  uint16_t* vhi;
-  uint16_t* rowpref;   // T + 1
-  int T;
-};
-
-// Columns v of row u with key <= h, knowing that the first `from` qualify.
-__device__ __forceinline__ int row_count(const Lists& S, int u, int from, uint32_t h) {
-  const float a = S.s1[u];
-  int lo = from, hi = S.T;  // first v with key > h lies in [lo, hi]
+// Columns v < P2 of a row with distance a whose key is <= h, knowing that the
+// first `from` qualify.
+__device__ __forceinline__ int row_count(const float* s2, int P2, float a, int from, uint32_t h) {
+  int lo = from, hi = P2;  // first v with key > h lies in [lo, hi]
   while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (f2ord(__fadd_rn(a, S.s2[mid])) <= h)
+    const int mid = (lo + hi) >> 1;
+    if (f2ord(__fadd_rn(a, s2[mid])) <= h)
       lo = mid + 1;
     else
       hi = mid;
   }
   return lo;
-}
-
-// Cells with tau_lo < key <= h (all rows).  Rows whose next cell is above h add nothing.
-__device__ long long count_band(const Lists& S, uint32_t h, Red& r) {
-  long long c = 0;
-  for (int u = threadIdx.x; u < S.T; u += NT) {
-    const int v = S.vlo[u];
-    if (v < S.T && f2ord(__fadd_rn(S.s1[u], S.s2[v])) <= h) c += row_count(S, u, v + 1, h) - v;
-  }
-  return block_sum(c, r);
-}
-
-constexpr int NTH = 8;  // thresholds evaluated per block reduction
-
-// Band cell counts for NTH ascending thresholds h[0..NTH) at once; the results
-// land in out[0..NTH) on every thread.
-__device__ void count_band_multi(const Lists& S, const uint32_t* h, long long* out, long long (*red8)[NTH]) {
-  long long c[NTH];
-#pragma unroll
-  for (int j = 0; j < NTH; ++j) c[j] = 0;
-  for (int u = threadIdx.x; u < S.T; u += NT) {
-    const int v = S.vlo[u];
-    if (v >= S.T) continue;
-    const uint32_t kf = f2ord(__fadd_rn(S.s1[u], S.s2[v]));
-    if (kf > h[NTH - 1]) continue;
-#pragma unroll
-    for (int j = 0; j < NTH; ++j)
-      if (kf <= h[j]) c[j] += row_count(S, u, v + 1, h[j]) - v;
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-#pragma unroll
-  for (int j = 0; j < NTH; ++j) c[j] = warp_sum(c[j]);
-  __syncthreads();
-  if (l == 0)
-#pragma unroll
-    for (int j = 0; j < NTH; ++j) red8[w][j] = c[j];
-  __syncthreads();
-  if (threadIdx.x < NTH) {
-    long long t = 0;
-    for (int x = 0; x < NW; ++x) t += red8[x][threadIdx.x];
-    red8[NW][threadIdx.x] = t;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < NTH; ++j) out[j] = red8[NW][j];
 }
 
 // Smallest key v (as ord bits) among the band entries such that the points of
@@ -305,202 +308,317 @@ __device__ uint32_t weighted_select(const uint64_t* band, const uint32_t* cnt, i
   return prefix;
 }
 
-__global__ void __launch_bounds__(NT) traverse_kernel(TraverseArgs a) {
+// Shared-memory layout of one CTA, for T coarse codewords per half.
+struct Layout {
+  size_t u_bytes;  // union: radix scratch | sort buffer | band
+  size_t total;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline Layout smem_layout(int T) {
+  int TP = 1;
+  while (TP < T) TP <<= 1;
+  Layout l;
+  const size_t radix = (size_t)TP * 12 + (size_t)(NW + 1) * 256 * 4;
+  l.u_bytes = align16(max(radix, (size_t)8 * max(ECAP, TP)));
+  // bcnt[ECAP] u32, s1[T] f32, s2[T] f32, afk[T] u32, p2/vlo/arow/vhic[T] u16, rowpref[T+1] u16
+  l.total = l.u_bytes + (size_t)ECAP * 4 + (size_t)T * 12 + (size_t)T * 8 + (size_t)(T + 1) * 2 + 16;
+  return l;
+}
+
+__global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Red red;
-  __shared__ int nband_s;
-  __shared__ int nout_s;
+  __shared__ int nband_s, nout_s, na_s, cnt_s;
   __shared__ long long emit_pts_s;
+  __shared__ uint32_t h_s, theta_s, ovf_s;
   __shared__ unsigned long long hist[258];
-  __shared__ long long red8[NW + 1][NTH];
   const float rho = a.rho;
   const int T = a.T;
   int TP = 1;
   while (TP < T) TP <<= 1;
-  // shared layout: [sort scratch | band (union)][bcnt][s1 s2][p2 vlo vhi rowpref]
-  const size_t sort_bytes = (size_t)TP * 12 + (size_t)(NW + 1) * 256 * 4;
-  const size_t union_bytes = (max(sort_bytes, (size_t)8 * ECAP) + 15) & ~(size_t)15;
+  const Layout lay = smem_layout(T);
+  // union region
   uint32_t* sk = reinterpret_cast<uint32_t*>(smem);
   uint32_t* sk2 = sk + TP;
   uint16_t* sv = reinterpret_cast<uint16_t*>(sk2 + TP);
   uint16_t* sv2 = sv + TP;
   uint32_t* srun = reinterpret_cast<uint32_t*>(sv2 + TP);
   uint32_t* swc = srun + 256;
-  uint64_t* band = reinterpret_cast<uint64_t*>(smem);
-  uint32_t* bcnt = reinterpret_cast<uint32_t*>(smem + union_bytes);
+  uint64_t* band = reinterpret_cast<uint64_t*>(smem);  // also the column sort buffer
+  // fixed region
+  uint32_t* bcnt = reinterpret_cast<uint32_t*>(smem + lay.u_bytes);
   float* s1 = reinterpret_cast<float*>(bcnt + ECAP);
   float* s2 = s1 + T;
-  uint16_t* p2 = reinterpret_cast<uint16_t*>(s2 + T);
-  Lists S;
-  S.T = T;
-  S.s1 = s1;
-  S.s2 = s2;
-  S.p2 = p2;
-  S.vlo = p2 + T;
-  S.vhi = S.vlo + T;
-  S.rowpref = S.vhi + T;
+  uint32_t* afk = reinterpret_cast<uint32_t*>(s2 + T);
+  uint16_t* p2 = reinterpret_cast<uint16_t*>(afk + T);
+  uint16_t* vlo = p2 + T;
+  uint16_t* arow = vlo + T;
+  uint16_t* vhic = arow + T;
+  uint16_t* rowpref = vhic + T;  // T + 1
+  // d2 ord keys live in a copy outside the union while the prefix is built
+  uint32_t* dk = afk;
 
   for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
     const int64_t L = a.L ? (int64_t)a.L[q] : (int64_t)a.L_scalar;
     const float* d1 = a.d1 + q * T;
     const float* d2 = a.d2 + q * T;
-    // 1. rows as they are; columns sorted by (distance, index)
     __syncthreads();
-    float s1min = __int_as_float(0x7f800000), s1max = -__int_as_float(0x7f800000);
-    int argmin = 0;
-    uint32_t kmin = 0xffffffffu, kmax = 0u;
+    float m1 = __int_as_float(0x7f800000);
     for (int t = threadIdx.x; t < T; t += NT) {
-      const uint32_t kk = f2ord(d2[t]);
-      sk[t] = kk;
-      kmin = min(kmin, kk);
-      kmax = max(kmax, kk);
-      sv[t] = (uint16_t)t;
       const float x = d1[t];
       s1[t] = x;
-      S.vlo[t] = 0;
-      if (x < s1min) {
-        s1min = x;
-        argmin = t;
+      m1 = fminf(m1, x);
+      dk[t] = f2ord(d2[t]);
+      vlo[t] = 0;
+    }
+    const float min1 = ord2f(block_min_u32(f2ord(m1), red));
+    // 1. sorted prefix of the columns
+    int P2;
+    uint32_t limit;  // every key >= limit lies outside the sorted prefix
+    bool full = false;
+    if (T > 1024) {
+      full = true;
+    } else {
+      uint32_t theta = ORD_INF;
+      if (T > 256) {
+        // sample every (TP/256)-th column; theta = a low quantile of the sample
+        const int stride = TP / 256;
+        const int srank = (L <= (int64_t)(2048.f * fmaxf(rho, 1.f))) ? 63 : 127;
+        if (threadIdx.x < 32) {
+          uint64_t x[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int col = (threadIdx.x * 8 + i) * stride;
+            x[i] = col < T ? ((uint64_t)dk[col] << 32) : ~0ull;
+          }
+          warp_sort<8>(x);
+          // element srank sits in lane srank / 8, slot srank % 8
+          const uint64_t pick = __shfl_sync(0xffffffffu, x[srank % 8], srank / 8);
+          if (threadIdx.x == 0) theta_s = (uint32_t)(pick >> 32);
+        }
+        __syncthreads();
+        theta = theta_s;
       }
-      s1max = fmaxf(s1max, x);
+      // compact the columns with key <= theta, then warp 0 sorts them
+      if (threadIdx.x == 0) cnt_s = 0;
+      __syncthreads();
+      for (int t0 = 0; t0 < T; t0 += NT) {
+        const int t = t0 + threadIdx.x;
+        const bool take = t < T && dk[t] <= theta;
+        const uint32_t m = __ballot_sync(0xffffffffu, take);
+        int at = 0;
+        if ((threadIdx.x & 31) == 0 && m) at = atomicAdd(&cnt_s, __popc(m));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (take) band[at + __popc(m & lanemask_lt())] = ((uint64_t)dk[t] << 32) | (uint32_t)t;
+      }
+      __syncthreads();
+      P2 = cnt_s;
+      if (P2 <= 256) {
+        if (threadIdx.x < 32) warp_sort_buf(band, P2);
+        __syncthreads();
+      } else {  // larger prefixes: block-wide bitonic sort
+        int n2 = 2;
+        while (n2 < P2) n2 <<= 1;
+        for (int t = P2 + threadIdx.x; t < n2; t += NT) band[t] = ~0ull;
+        block_bitonic_sort(band, n2);
+      }
+      for (int t = threadIdx.x; t < P2; t += NT) {
+        const uint64_t e = band[t];
+        s2[t] = ord2f((uint32_t)(e >> 32));
+        p2[t] = (uint16_t)(uint32_t)e;
+      }
+      limit = (theta == ORD_INF) ? ORD_INF : f2ord(__fadd_rn(min1, ord2f(theta)));
     }
-    kmin = block_min_u32(kmin, red);
-    kmax = 0xffffffffu - block_min_u32(0xffffffffu - kmax, red);
-    block_radix_sort(sk, sv, sk2, sv2, T, kmin, kmax, srun, swc);
-    for (int t = threadIdx.x; t < T; t += NT) {
-      s2[t] = ord2f(sk[t]);
-      p2[t] = sv[t];
+    if (full) {
+      for (int t = threadIdx.x; t < T; t += NT) {
+        sk[t] = dk[t];
+        sv[t] = (uint16_t)t;
+      }
+      __syncthreads();
+      block_radix_sort(sk, sv, sk2, sv2, T, srun, swc);
+      for (int t = threadIdx.x; t < T; t += NT) {
+        s2[t] = ord2f(sk[t]);
+        p2[t] = sv[t];
+      }
+      P2 = T;
+      limit = ORD_INF;
     }
-    // the row with the smallest d1 (lowest index among ties) and the largest key
-    const uint32_t mn = block_min_u32(f2ord(s1min), red);
-    const uint32_t rmin = block_min_u32(f2ord(s1min) == mn ? (uint32_t)argmin : 0xffffffffu, red);
-    const uint32_t s1max_ord = 0xffffffffu - block_min_u32(0xffffffffu - f2ord(s1max), red);
-    const uint32_t max_ord = f2ord(__fadd_rn(ord2f(s1max_ord), s2[T - 1]));
+    __syncthreads();
+
     long long committed = 0;  // points of the emitted cells
     int nout = 0;
     bool overflow = false;
     int target = (int)fminf((float)ECAP, fmaxf(32.f, ceilf((float)L / fmaxf(rho, 1.f))));
     bool done = false;
     while (!done) {
-      // 2. the band's upper key
-      uint32_t fr = 0xffffffffu;
+      // 2. the smallest frontier key and its row
+      unsigned long long fm = ~0ull;
       for (int u = threadIdx.x; u < T; u += NT) {
-        const int v = S.vlo[u];
-        if (v < T) fr = min(fr, f2ord(__fadd_rn(s1[u], s2[v])));
+        const int v = vlo[u];
+        if (v < P2) fm = min(fm, ((unsigned long long)f2ord(__fadd_rn(s1[u], s2[v])) << 32) | (uint32_t)u);
       }
-      const uint32_t hmin = block_min_u32(fr, red);
-      if (hmin == 0xffffffffu) break;  // every cell visited
-      uint32_t h;
-      const long long cmin = count_band(S, hmin, red);
-      if (cmin > target) {
-        if (cmin > ECAP) {  // one tie group larger than the band
-          overflow = true;
-          break;
+      fm = block_min_u64(fm, red);
+      const uint32_t hmin = (uint32_t)(fm >> 32);
+      if (fm == ~0ull || hmin >= limit) {
+        if (P2 < T) {  // the prefix is used up: sort every column and go on
+          for (int t = threadIdx.x; t < T; t += NT) {
+            sk[t] = f2ord(d2[t]);
+            sv[t] = (uint16_t)t;
+          }
+          __syncthreads();
+          block_radix_sort(sk, sv, sk2, sv2, T, srun, swc);
+          for (int t = threadIdx.x; t < T; t += NT) {
+            s2[t] = ord2f(sk[t]);
+            p2[t] = sv[t];
+          }
+          P2 = T;
+          limit = ORD_INF;
+          __syncthreads();
+          continue;
         }
-        h = hmin;
-      } else {
-        // bracket [lo, hi] with count(lo) <= target < count(hi)
-        uint32_t lo = hmin, hi = max_ord;
-        long long clo = cmin, chi = -1;
-        {  // first guess: `target` more cells in the row with the smallest d1
-          const int vr = min(T - 1, (int)S.vlo[rmin] + target);
-          const uint32_t g = f2ord(__fadd_rn(s1[rmin], s2[vr]));
-          if (g > lo && g < hi) {
-            const long long cg = count_band(S, g, red);
-            if (cg <= target) {
-              lo = g;
-              clo = cg;
-            } else {
-              hi = g;
-              chi = cg;
-            }
-          }
-        }
-        if (chi < 0) {
-          chi = count_band(S, hi, red);
-          if (chi <= target) {
-            lo = hi;
-            clo = chi;
-          }
-        }
-        // each round evaluates NTH thresholds spread around the interpolated one
-        // (counts grow like the square of the key inside a staircase)
-        while (hi - lo > 1 && 2 * clo < target) {
-          const float flo = ord2f(lo), fhi = ord2f(hi);
-          const float sl = sqrtf((float)clo), sh = sqrtf((float)chi), sa = sqrtf(0.75f * (float)target);
-          const float est = fminf(fmaxf((sa - sl) / fmaxf(sh - sl, 1e-6f), 0.02f), 0.98f);
-          const float spread[NTH] = {0.35f, 0.55f, 0.75f, 0.9f, 1.0f, 1.12f, 1.3f, 1.6f};
-          uint32_t th[NTH];
-          uint32_t prev = lo;
-#pragma unroll
-          for (int j = 0; j < NTH; ++j) {
-            uint32_t t = f2ord(flo + fminf(est * spread[j], 0.999f) * (fhi - flo));
-            if (t <= prev) t = prev + 1;
-            if (t >= hi) t = hi - 1;
-            th[j] = max(t, prev);
-            prev = th[j];
-          }
-          if (hi - lo <= (uint32_t)NTH + 1) {  // narrow bracket: every key in it
-#pragma unroll
-            for (int j = 0; j < NTH; ++j) th[j] = min(hi - 1, lo + 1 + j);
-          }
-          long long cnt[NTH];
-          count_band_multi(S, th, cnt, red8);
-          int best = -1;
-#pragma unroll
-          for (int j = 0; j < NTH; ++j)
-            if (cnt[j] <= target) best = j;
-          if (best >= 0) {
-            lo = th[best];
-            clo = cnt[best];
-          }
-          for (int j = NTH - 1; j > best; --j) {
-            if (th[j] > lo) {
-              hi = th[j];
-              chi = cnt[j];
-            }
-          }
-        }
-        h = lo;
+        break;  // every cell visited
       }
-      // 3. enumerate the band: rows u, columns [vlo[u], vhi[u])
-      for (int u = threadIdx.x; u < T; u += NT) {
-        const int vl = S.vlo[u];
-        S.vhi[u] = (uint16_t)((vl < T && f2ord(__fadd_rn(s1[u], s2[vl])) <= h) ? row_count(S, u, vl + 1, h) : vl);
+      const int rowh = (int)(uint32_t)fm;
+      // upper guess: `target` more columns in the row with the smallest frontier key
+      const uint32_t lim1 = limit == ORD_INF ? ORD_INF - 1 : limit - 1;
+      const uint32_t g_hi =
+          min(lim1, f2ord(__fadd_rn(s1[rowh], s2[min(P2 - 1, (int)vlo[rowh] + target)])));
+      const uint32_t g1 = min(
+          g_hi, f2ord(__fadd_rn(s1[rowh], s2[min(P2 - 1, (int)vlo[rowh] + (int)ceilf(sqrtf(2.f * target)))])));
+      // rows whose next cell is <= g_hi
+      if (threadIdx.x == 0) na_s = 0;
+      __syncthreads();
+      for (int u0 = 0; u0 < T; u0 += NT) {
+        const int u = u0 + threadIdx.x;
+        uint32_t fk = ORD_INF;
+        if (u < T && vlo[u] < P2) fk = f2ord(__fadd_rn(s1[u], s2[vlo[u]]));
+        const bool take = fk <= g_hi;
+        const uint32_t m = __ballot_sync(0xffffffffu, take);
+        int at = 0;
+        if ((threadIdx.x & 31) == 0 && m) at = atomicAdd(&na_s, __popc(m));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (take) {
+          const int i = at + __popc(m & lanemask_lt());
+          arow[i] = (uint16_t)u;
+          afk[i] = fk;
+        }
       }
       __syncthreads();
-      {  // exclusive prefix of the band lengths over rows
-        const int per = (T + NT - 1) / NT;
+      const int na = na_s;
+      // warp 0: the band's upper key
+      if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        auto count = [&](uint32_t h) -> long long {
+          long long c = 0;
+          for (int i = lane; i < na; i += 32) {
+            if (afk[i] <= h) {
+              const int u = arow[i], v = vlo[u];
+              c += row_count(s2, P2, s1[u], v + 1, h) - v;
+            }
+          }
+          return warp_sum(c);
+        };
+        const long long cap = ECAP;
+        const long long lo_ok = max(1, target / 2), hi_ok = min(cap, 2LL * target);
+        uint32_t h = 0;
+        bool ovf = false;
+        const long long cmin = count(hmin);
+        if (cmin > cap) {
+          ovf = true;  // one tie group larger than the band
+        } else {
+          uint32_t lo = hmin, hi = g_hi;
+          long long clo = cmin, chi = -1;
+          const long long c1 = (g1 > hmin) ? count(g1) : cmin;
+          if (c1 <= hi_ok) {
+            lo = g1;
+            clo = c1;
+          } else {
+            hi = g1;
+            chi = c1;
+          }
+          if (chi < 0) {
+            chi = (g_hi > lo) ? count(g_hi) : clo;
+            if (chi <= hi_ok) {  // the whole guess fits: take it
+              lo = g_hi;
+              clo = chi;
+            }
+          }
+          int it = 0;
+          while (hi > lo + 1 && clo < lo_ok && chi > hi_ok) {
+            uint32_t mid;
+            if (it < 8) {
+              const float flo = ord2f(lo), fhi = ord2f(hi);
+              const float sl = sqrtf((float)clo), sh = sqrtf((float)chi), sa = sqrtf(1.2f * (float)target);
+              const float frac = fminf(fmaxf((sa - sl) / fmaxf(sh - sl, 1e-6f), 0.02f), 0.98f);
+              mid = f2ord(flo + frac * (fhi - flo));
+              if (mid <= lo) mid = lo + 1;
+              if (mid >= hi) mid = hi - 1;
+            } else {
+              mid = lo + ((hi - lo) >> 1);
+            }
+            ++it;
+            const long long c = count(mid);
+            if (c <= hi_ok) {
+              lo = mid;
+              clo = c;
+            } else {
+              hi = mid;
+              chi = c;
+            }
+          }
+          h = lo;
+        }
+        if (lane == 0) {
+          h_s = h;
+          ovf_s = ovf ? 1u : 0u;
+        }
+      }
+      __syncthreads();
+      if (ovf_s) {
+        overflow = true;
+        break;
+      }
+      const uint32_t h = h_s;
+      // 3. enumerate the band over the compacted rows
+      for (int i = threadIdx.x; i < na; i += NT) {
+        const int u = arow[i], v = vlo[u];
+        vhic[i] = (uint16_t)((afk[i] <= h) ? row_count(s2, P2, s1[u], v + 1, h) : v);
+      }
+      __syncthreads();
+      {  // exclusive prefix of the band lengths over the compacted rows
+        const int per = (na + NT - 1) / NT;
         const int r0 = threadIdx.x * per;
         long long loc = 0;
-        for (int u = r0; u < min(T, r0 + per); ++u) loc += S.vhi[u] - S.vlo[u];
+        for (int i = r0; i < min(na, r0 + per); ++i) loc += vhic[i] - vlo[arow[i]];
         long long tot;
         const long long incl = block_incl_scan(loc, red, &tot);
         long long run = incl - loc;
-        for (int u = r0; u < min(T, r0 + per); ++u) {
-          S.rowpref[u] = (uint16_t)run;
-          run += S.vhi[u] - S.vlo[u];
+        for (int i = r0; i < min(na, r0 + per); ++i) {
+          rowpref[i] = (uint16_t)run;
+          run += vhic[i] - vlo[arow[i]];
         }
         if (threadIdx.x == 0) {
-          S.rowpref[T] = (uint16_t)tot;
+          rowpref[na] = (uint16_t)tot;
           nband_s = 0;
           nout_s = 0;
         }
       }
       __syncthreads();
-      const int E = S.rowpref[T];
+      const int E = rowpref[na];
       long long pts = 0;
       for (int e = threadIdx.x; e < E; e += NT) {
-        int lo = 0, hi = T;  // last row with rowpref <= e
+        int lo = 0, hi = na;  // last compacted row with rowpref <= e
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
-          if (S.rowpref[mid] <= e)
+          if (rowpref[mid] <= e)
             lo = mid;
           else
             hi = mid;
         }
-        const int u = lo;
-        const int v = S.vlo[u] + (e - S.rowpref[u]);
+        const int u = arow[lo];
+        const int v = vlo[u] + (e - rowpref[lo]);
         const uint32_t cell = (uint32_t)u * (uint32_t)T + (uint32_t)p2[v];
         const uint32_t b = a.offsets[cell];
         const uint32_t n = a.offsets[cell + 1] - b;
@@ -515,8 +633,8 @@ __global__ void __launch_bounds__(NT) traverse_kernel(TraverseArgs a) {
       const long long band_pts = block_sum(pts, red);
       const int nb = nband_s;
       const long long need = L - committed;
-      const bool last = band_pts >= need || h == max_ord;
       bpq_cell* out = a.cells + q * (int64_t)a.cap;
+      bool last = band_pts >= need;
       if (a.ordered) {
         // 4a. sorted band; cut at the first cell whose running count reaches L
         int n2 = 2;
@@ -537,9 +655,9 @@ __global__ void __launch_bounds__(NT) traverse_kernel(TraverseArgs a) {
             }
             long long tot;
             const long long incl = block_incl_scan(x, red, &tot);
-            const uint32_t cand = (c < nb && run + incl >= need) ? (uint32_t)c : 0xffffffffu;
+            const uint32_t cand = (c < nb && run + incl >= need) ? (uint32_t)c : ORD_INF;
             const uint32_t first = block_min_u32(cand, red);
-            if (first != 0xffffffffu) {
+            if (first != ORD_INF) {
               emit = (int)first + 1;
               if ((uint32_t)c == first) emit_pts_s = run + incl;
               __syncthreads();
@@ -591,14 +709,14 @@ __global__ void __launch_bounds__(NT) traverse_kernel(TraverseArgs a) {
         uint32_t lastcell = 0;
         bool first_tie = true;
         while (got < need) {
-          uint32_t cand = 0xffffffffu;
+          uint32_t cand = ORD_INF;
           for (int t = threadIdx.x; t < nb; t += NT) {
             const uint64_t e = band[t];
             const uint32_t cell = (uint32_t)e;
             if ((uint32_t)(e >> 32) == vcut && (first_tie || cell > lastcell)) cand = min(cand, cell);
           }
           const uint32_t c = block_min_u32(cand, red);
-          if (c == 0xffffffffu) break;  // not reached: the tied cells hold the remaining points
+          if (c == ORD_INF) break;  // not reached: the tied cells hold the remaining points
           const uint32_t b = a.offsets[c];
           const uint32_t n = a.offsets[c + 1] - b;
           if (threadIdx.x == 0 && nout + added < a.cap) out[nout + added] = bpq_cell{c, b, n, ord2f(vcut)};
@@ -616,7 +734,7 @@ __global__ void __launch_bounds__(NT) traverse_kernel(TraverseArgs a) {
       }
       if (last) done = true;
       // next band
-      for (int u = threadIdx.x; u < T; u += NT) S.vlo[u] = S.vhi[u];
+      for (int i = threadIdx.x; i < na; i += NT) vlo[arow[i]] = vhic[i];
       target = min(ECAP, 2 * target);
       __syncthreads();
     }
@@ -628,14 +746,6 @@ __global__ void __launch_bounds__(NT) traverse_kernel(TraverseArgs a) {
   }
 }
 
-size_t traverse_smem(int T) {
-  int TP = 1;
-  while (TP < T) TP <<= 1;
-  const size_t sort_bytes = (size_t)TP * 12 + (size_t)(NW + 1) * 256 * 4;
-  const size_t union_bytes = (std::max(sort_bytes, (size_t)8 * ECAP) + 15) & ~(size_t)15;
-  return union_bytes + (size_t)ECAP * 4 + (size_t)T * 8 + (size_t)(4 * T + 1) * 2;
-}
-
 }  // namespace
 
 int traverse_band_capacity() { return ECAP; }
@@ -643,7 +753,8 @@ int traverse_band_capacity() { return ECAP; }
 void launch_traverse(const TraverseArgs& a, cudaStream_t st) {
   if (a.nq <= 0) return;
   BPQ_CHECK(a.T >= 1 && a.T <= MAX_T, BPQ_EINVAL, "T out of range for the traversal");
-  const size_t smem = traverse_smem(a.T);
+  const size_t smem = smem_layout(a.T).total;
+  BPQ_CHECK(smem <= 227 * 1024, BPQ_EINVAL, "T too large for the traversal's shared memory");
   BPQ_CUDA(cudaFuncSetAttribute(traverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
   traverse_kernel<<<grid, NT, smem, st>>>(a);
