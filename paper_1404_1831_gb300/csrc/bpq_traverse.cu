@@ -327,7 +327,11 @@ __host__ __device__ inline Layout smem_layout(int T) {
   return l;
 }
 
-__global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a) {
+// The general path: one CTA per query.  With only_marked, it takes only the
+// queries the warp kernel could not finish (ncells == FALLBACK).
+constexpr int FALLBACK = -2;
+
+__global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a, int only_marked) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Red red;
   __shared__ int nband_s, nout_s, na_s, cnt_s;
@@ -361,6 +365,7 @@ __global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a) {
   uint32_t* dk = afk;
 
   for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
+    if (only_marked && a.ncells[q] != FALLBACK) continue;  // uniform across the CTA
     const int64_t L = a.L ? (int64_t)a.L[q] : (int64_t)a.L_scalar;
     const float* d1 = a.d1 + q * T;
     const float* d2 = a.d2 + q * T;
@@ -746,6 +751,327 @@ __global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a) {
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// The common path: one warp per query, no block-wide barriers.
+//  * a sample of d2 gives theta2; the columns with d2 <= theta2 (at most PCAP)
+//    are compacted and sorted in registers, and the rows with
+//    d1 <= min(d1) + theta2 - min(d2) (at most RCAP) are compacted.  Every cell
+//    outside this row x column grid has a key of at least the limit
+//    min(min(d1) + theta2, theta1 + min(d2)), so bands stay below it;
+//  * each band holds at most BCAP cells: its edge is searched with warp-wide
+//    counts, its cells are enumerated and sorted by (key, cell id) in registers,
+//    and the non-empty ones are emitted in that order up to the cut, so the
+//    output is always the exact visit order.
+// A query that needs more than the grid, or a tie group larger than a band, is
+// marked FALLBACK and finished by the CTA kernel.
+// ---------------------------------------------------------------------------
+constexpr int WPB = 4;      // warps (queries) per CTA
+constexpr int PCAP = 256;   // sorted column prefix
+constexpr int RCAP = 256;   // row prefix
+constexpr int BCAP = 256;   // band cells
+
+struct WarpSmem {
+  uint64_t band[BCAP];  // also the column compaction buffer
+  float cs2[PCAP];
+  float rs1[RCAP];
+  uint32_t rfk[RCAP];   // frontier key per row (ord bits), ORD_INF when the row is used up
+  uint16_t cp2[PCAP];
+  uint16_t rid[RCAP];
+  uint16_t rvlo[RCAP];
+  uint16_t rvhi[RCAP];
+};
+
+__device__ __forceinline__ uint32_t warp_min_u32(uint32_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_excl_scan(V x, V* total) {
+  const int l = threadIdx.x & 31;
+  V v = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const V y = __shfl_up_sync(0xffffffffu, v, o);
+    if (l >= o) v += y;
+  }
+  *total = __shfl_sync(0xffffffffu, v, 31);
+  return v - x;
+}
+
+__global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs a) {
+  __shared__ WarpSmem smw[WPB];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpSmem& W = smw[warp];
+  const int T = a.T;
+  int TP = 1;
+  while (TP < T) TP <<= 1;
+  const float rho = fmaxf(a.rho, 1.f);
+  for (int64_t q = (int64_t)blockIdx.x * WPB + warp; q < a.nq; q += (int64_t)gridDim.x * WPB) {
+    const int64_t L = a.L ? (int64_t)a.L[q] : (int64_t)a.L_scalar;
+    const float* d1 = a.d1 + q * T;
+    const float* d2 = a.d2 + q * T;
+    __syncwarp();
+    // minima of both lists
+    uint32_t m1 = ORD_INF, m2 = ORD_INF;
+    for (int t = lane; t < T; t += 32) {
+      m1 = min(m1, f2ord(d1[t]));
+      m2 = min(m2, f2ord(d2[t]));
+    }
+    const float min1 = ord2f(warp_min_u32(m1)), min2 = ord2f(warp_min_u32(m2));
+    // column threshold from a sample of 256 columns
+    uint32_t th2 = ORD_INF;
+    if (T > PCAP) {
+      const int stride = TP / 256;
+      uint64_t x[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int col = (lane * 8 + i) * stride;
+        x[i] = col < T ? ((uint64_t)f2ord(d2[col]) << 32) : ~0ull;
+      }
+      warp_sort<8>(x);
+      // about 2 sqrt(L / rho) columns, at most half the prefix capacity
+      const float want = fminf((float)PCAP * 0.5f, fmaxf(32.f, 2.f * sqrtf((float)L / rho)));
+      const int sr = min(255, max(0, (int)(want / (float)stride) - 1));
+      th2 = (uint32_t)(__shfl_sync(0xffffffffu, x[sr & 7], sr >> 3) >> 32);
+    }
+    bool fb = false;
+    // compact the columns with d2 <= theta2
+    int P2 = 0;
+    for (int t0 = 0; t0 < T; t0 += 32) {
+      const int t = t0 + lane;
+      const uint32_t key = t < T ? f2ord(d2[t]) : ORD_INF;
+      const bool take = t < T && key <= th2;
+      const uint32_t m = __ballot_sync(0xffffffffu, take);
+      const int pos = P2 + __popc(m & lanemask_lt());
+      if (take && pos < PCAP) W.band[pos] = ((uint64_t)key << 32) | (uint32_t)t;
+      P2 += __popc(m);
+    }
+    if (P2 > PCAP) fb = true;
+    // rows with d1 <= theta1 = min1 + theta2 - min2
+    uint32_t limit = ORD_INF, th1 = ORD_INF;
+    if (th2 != ORD_INF) {
+      const float th2f = ord2f(th2);
+      const float th1f = min1 + (th2f - min2);
+      th1 = f2ord(th1f);
+      limit = min(f2ord(__fadd_rn(min1, th2f)), f2ord(__fadd_rn(th1f, min2)));
+    }
+    int R = 0;
+    for (int t0 = 0; t0 < T; t0 += 32) {
+      const int t = t0 + lane;
+      const float dv = t < T ? d1[t] : 0.f;
+      const bool take = t < T && f2ord(dv) <= th1;
+      const uint32_t m = __ballot_sync(0xffffffffu, take);
+      const int pos = R + __popc(m & lanemask_lt());
+      if (take && pos < RCAP) {
+        W.rs1[pos] = dv;
+        W.rid[pos] = (uint16_t)t;
+        W.rvlo[pos] = 0;
+      }
+      R += __popc(m);
+    }
+    if (R > RCAP) fb = true;
+    __syncwarp();
+    if (!fb) {
+      warp_sort_buf(W.band, P2);
+      __syncwarp();
+      for (int v = lane; v < P2; v += 32) {
+        const uint64_t e = W.band[v];
+        W.cs2[v] = ord2f((uint32_t)(e >> 32));
+        W.cp2[v] = (uint16_t)(uint32_t)e;
+      }
+      __syncwarp();
+      for (int r = lane; r < R; r += 32) W.rfk[r] = f2ord(__fadd_rn(W.rs1[r], W.cs2[0]));
+      __syncwarp();
+    }
+    long long committed = 0;
+    int nout = 0;
+    bool overflow = false;
+    bpq_cell* out = a.cells + q * (int64_t)a.cap;
+    while (!fb) {
+      // smallest frontier key
+      unsigned long long fm = ~0ull;
+      for (int r = lane; r < R; r += 32) {
+        const uint32_t f = W.rfk[r];
+        if (f != ORD_INF) fm = min(fm, ((unsigned long long)f << 32) | (uint32_t)r);
+      }
+      fm = warp_min_u64(fm);
+      const uint32_t hmin = (uint32_t)(fm >> 32);
+      if (fm == ~0ull || hmin >= limit) {
+        if (limit != ORD_INF) fb = true;  // the grid is used up before the budget
+        break;                            // else: every cell visited
+      }
+      const int rh = (int)(uint32_t)fm;
+      auto count = [&](uint32_t h) -> long long {
+        long long c = 0;
+        for (int r = lane; r < R; r += 32) {
+          if (W.rfk[r] <= h) {
+            const int v = W.rvlo[r];
+            c += row_count(W.cs2, P2, W.rs1[r], v + 1, h) - v;
+          }
+        }
+        return warp_sum(c);
+      };
+      const long long cmin = count(hmin);
+      if (cmin > BCAP) {  // a tie group larger than a band
+        fb = true;
+        break;
+      }
+      const uint32_t lim1 = limit == ORD_INF ? ORD_INF - 1 : limit - 1;
+      const int vh = W.rvlo[rh];
+      const float sh = W.rs1[rh];
+      const uint32_t g_hi = min(lim1, f2ord(__fadd_rn(sh, W.cs2[min(P2 - 1, vh + BCAP)])));
+      const uint32_t g1 = min(g_hi, f2ord(__fadd_rn(sh, W.cs2[min(P2 - 1, vh + 16)])));
+      const long long lo_ok = BCAP / 2, hi_ok = BCAP;
+      uint32_t lo = hmin, hi = g_hi;
+      long long clo = cmin, chi = -1;
+      {
+        const long long c1 = (g1 > hmin) ? count(g1) : cmin;
+        if (c1 <= hi_ok) {
+          lo = g1;
+          clo = c1;
+        } else {
+          hi = g1;
+          chi = c1;
+        }
+        if (chi < 0) {
+          chi = (g_hi > lo) ? count(g_hi) : clo;
+          if (chi <= hi_ok) {
+            lo = g_hi;
+            clo = chi;
+          }
+        }
+        int it = 0;
+        while (hi > lo + 1 && clo < lo_ok && chi > hi_ok) {
+          uint32_t mid;
+          if (it < 8) {
+            const float flo = ord2f(lo), fhi = ord2f(hi);
+            const float sl = sqrtf((float)clo), shh = sqrtf((float)chi), sa = sqrtf(0.75f * (float)BCAP);
+            const float frac = fminf(fmaxf((sa - sl) / fmaxf(shh - sl, 1e-6f), 0.02f), 0.98f);
+            mid = f2ord(flo + frac * (fhi - flo));
+            if (mid <= lo) mid = lo + 1;
+            if (mid >= hi) mid = hi - 1;
+          } else {
+            mid = lo + ((hi - lo) >> 1);
+          }
+          ++it;
+          const long long c = count(mid);
+          if (c <= hi_ok) {
+            lo = mid;
+            clo = c;
+          } else {
+            hi = mid;
+            chi = c;
+          }
+        }
+      }
+      const uint32_t h = lo;
+      // the band's cells: columns [rvlo, rvhi) of every row
+      int loc = 0;
+      for (int r = lane; r < R; r += 32) {
+        const int v = W.rvlo[r];
+        const int vhi = (W.rfk[r] <= h) ? row_count(W.cs2, P2, W.rs1[r], v + 1, h) : v;
+        W.rvhi[r] = (uint16_t)vhi;
+        loc += vhi - v;
+      }
+      int E;
+      int pos = warp_excl_scan(loc, &E);
+      for (int r = lane; r < R; r += 32) {
+        const int v0 = W.rvlo[r], v1 = W.rvhi[r];
+        const uint32_t rowbase = (uint32_t)W.rid[r] * (uint32_t)T;
+        const float s1r = W.rs1[r];
+        for (int v = v0; v < v1; ++v)
+          W.band[pos++] = ((uint64_t)f2ord(__fadd_rn(s1r, W.cs2[v])) << 32) | (rowbase + W.cp2[v]);
+      }
+      __syncwarp();
+      // sort the band by (key, cell id); lane l holds entries 8l .. 8l + 7
+      uint64_t x[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int e = lane * 8 + i;
+        x[i] = e < E ? W.band[e] : ~0ull;
+      }
+      warp_sort<8>(x);
+      uint32_t cnt[8], beg[8];
+      long long mysum = 0;
+      int mynz = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        cnt[i] = 0;
+        beg[i] = 0;
+        if (lane * 8 + i < E) {
+          const uint32_t cell = (uint32_t)x[i];
+          beg[i] = a.offsets[cell];
+          cnt[i] = a.offsets[cell + 1] - beg[i];
+        }
+        mysum += cnt[i];
+        mynz += cnt[i] > 0;
+      }
+      long long band_pts;
+      long long before = warp_excl_scan(mysum, &band_pts);
+      const long long need = L - committed;
+      // the cut: first entry whose running count reaches need
+      int cut = E;  // entries [0, cut) are emitted
+      {
+        int mine = 1 << 30;
+        long long run = before;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          run += cnt[i];
+          if (mine == (1 << 30) && cnt[i] > 0 && run >= need) mine = lane * 8 + i;
+        }
+        const int first = (int)warp_min_u32((uint32_t)mine);
+        if (first != (1 << 30)) cut = first + 1;
+      }
+      // emit the non-empty entries before the cut, in order
+      int nzb = 0, nz_total;
+      {
+        int mine = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) mine += (lane * 8 + i < cut && cnt[i] > 0);
+        nzb = warp_excl_scan(mine, &nz_total);
+      }
+      if (nout + nz_total > a.cap) {
+        overflow = true;
+        break;
+      }
+      long long emitted_pts = 0;
+      {
+        int at = nout + nzb;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (lane * 8 + i < cut && cnt[i] > 0) {
+            out[at++] = bpq_cell{(uint32_t)x[i], beg[i], cnt[i], ord2f((uint32_t)(x[i] >> 32))};
+            emitted_pts += cnt[i];
+          }
+        }
+      }
+      emitted_pts = warp_sum(emitted_pts);
+      nout += nz_total;
+      committed += emitted_pts;
+      if (band_pts >= need) break;
+      // next band: advance every row to its band end
+      for (int r = lane; r < R; r += 32) {
+        const int v = W.rvhi[r];
+        W.rvlo[r] = (uint16_t)v;
+        W.rfk[r] = v < P2 ? f2ord(__fadd_rn(W.rs1[r], W.cs2[v])) : ORD_INF;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      if (fb) {
+        a.ncells[q] = FALLBACK;
+      } else {
+        a.ncells[q] = overflow ? -1 : nout;
+        a.npoints[q] = committed;
+        if (overflow) atomicExch(a.status, 1);
+      }
+    }
+  }
+}
+
 }  // namespace
 
 int traverse_band_capacity() { return ECAP; }
@@ -755,9 +1081,14 @@ void launch_traverse(const TraverseArgs& a, cudaStream_t st) {
   BPQ_CHECK(a.T >= 1 && a.T <= MAX_T, BPQ_EINVAL, "T out of range for the traversal");
   const size_t smem = smem_layout(a.T).total;
   BPQ_CHECK(smem <= 227 * 1024, BPQ_EINVAL, "T too large for the traversal's shared memory");
+  // common path: one warp per query
+  const int wgrid = (int)std::min<int64_t>((a.nq + WPB - 1) / WPB, 1 << 20);
+  traverse_warp_kernel<<<wgrid, WPB * 32, 0, st>>>(a);
+  check_launch("traverse warp kernel");
+  // queries the warp kernel marked: one CTA per query
   BPQ_CUDA(cudaFuncSetAttribute(traverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
-  traverse_kernel<<<grid, NT, smem, st>>>(a);
+  const int grid = (int)std::min<int64_t>(a.nq, 4096);
+  traverse_kernel<<<grid, NT, smem, st>>>(a, 1);
   check_launch("traverse kernel");
 }
 
