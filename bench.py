@@ -40,8 +40,8 @@ UNIT = "queries/s"
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--L", type=int, default=10_000)
     ap.add_argument("--k", type=int, default=100)
@@ -145,6 +145,15 @@ def oracle_sample_text(w, L, n):
 # ---------------------------------------------------------------------------
 # GPU side
 # ---------------------------------------------------------------------------
+def launches_per_step(w, scorer):
+    """Kernels one search launches: the query tables (one more for the LUT of the
+    table-based scorers), the traversal (its common path and the fallback pass
+    when T <= 1024) and the scan."""
+    tables = 2 if scorer in ("fbpq", "fbpq_tables") else 1
+    traverse = 2 if w.T <= 1024 else 1
+    return tables + traverse + 1
+
+
 class ClockSampler:
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -396,7 +405,7 @@ def run_ours(args):
                       "L": L, "k": k, "scorer": scorer, "codebooks": f"GPU k-means, {w.kmeans_iters} Lloyd "
                       f"iterations on {w.n_learn} learn points", "l2": "flushed between steps (512 MB write)",
                       "parallelism": f"replicas x{world} (independent query batches)"},
-           "roofline": roof, "gpu_launches": 4 * args.steps, "clocks": clocks,
+           "roofline": roof, "gpu_launches": launches_per_step(w, scorer) * args.steps, "clocks": clocks,
            "phases_ms": ph, "candidates_per_step": cand, "visited_cells_per_step": ncell_total,
            "index": {"n_points": info.n_points, "n_nonempty_cells": info.n_nonempty, "max_cell": info.max_cell},
            "e2e": e2e, "setup_s": round(setup_s, 1)}

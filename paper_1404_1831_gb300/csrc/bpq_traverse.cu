@@ -753,23 +753,26 @@ __global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a, int onl
 
 
 // ---------------------------------------------------------------------------
-// The common path: one warp per query, no block-wide barriers.
-//  * a sample of d2 gives theta2; the columns with d2 <= theta2 (at most PCAP)
-//    are compacted and sorted in registers, and the rows with
-//    d1 <= min(d1) + theta2 - min(d2) (at most RCAP) are compacted.  Every cell
-//    outside this row x column grid has a key of at least the limit
-//    min(min(d1) + theta2, theta1 + min(d2)), so bands stay below it;
+// The common path (T <= 1024): one warp per query, no block-wide barriers.
+//  * samples of d1 and d2 give thresholds theta1, theta2 for about `want` rows
+//    and columns; the columns with d2 <= theta2 (at most PCAP) are compacted and
+//    sorted in registers, and the rows with d1 <= theta1 (at most RCAP) are
+//    compacted.  Every cell outside this row x column grid has a key of at least
+//    the limit min(min(d1) + theta2, theta1 + min(d2)), so bands stay below it;
+//    when the budget is not reached below the limit the grid is rebuilt larger
+//    (rows keep their progress, kept per row id);
 //  * each band holds at most BCAP cells: its edge is searched with warp-wide
-//    counts, its cells are enumerated and sorted by (key, cell id) in registers,
-//    and the non-empty ones are emitted in that order up to the cut, so the
-//    output is always the exact visit order.
-// A query that needs more than the grid, or a tie group larger than a band, is
-// marked FALLBACK and finished by the CTA kernel.
+//    counts and its cells are enumerated.  The band that reaches the budget is
+//    sorted by (key, cell id) in registers and cut there; earlier bands are
+//    emitted whole, sorted only with `ordered` (the visit order is then exact).
+// A query whose grid would exceed the caps, or with a tie group larger than a
+// band, is marked FALLBACK and finished by the CTA kernel.
 // ---------------------------------------------------------------------------
 constexpr int WPB = 4;      // warps (queries) per CTA
 constexpr int PCAP = 256;   // sorted column prefix
 constexpr int RCAP = 256;   // row prefix
 constexpr int BCAP = 256;   // band cells
+constexpr int WARP_TMAX = 1024;
 
 struct WarpSmem {
   uint64_t band[BCAP];  // also the column compaction buffer
@@ -778,8 +781,8 @@ struct WarpSmem {
   uint32_t rfk[RCAP];   // frontier key per row (ord bits), ORD_INF when the row is used up
   uint16_t cp2[PCAP];
   uint16_t rid[RCAP];
-  uint16_t rvlo[RCAP];
   uint16_t rvhi[RCAP];
+  uint16_t vloid[WARP_TMAX];  // columns already visited, per row id
 };
 
 __device__ __forceinline__ uint32_t warp_min_u32(uint32_t x) {
@@ -801,6 +804,78 @@ __device__ __forceinline__ V warp_excl_scan(V x, V* total) {
   return v - x;
 }
 
+// Builds the row x column grid for about `want` rows and columns.  Returns false
+// if it would exceed the caps.
+__device__ bool build_grid(WarpSmem& W, const float* d1, const float* d2, int T, int TP, float want, float min1,
+                           float min2, int* P2out, int* Rout, uint32_t* limit) {
+  const int lane = threadIdx.x & 31;
+  uint32_t th1 = ORD_INF, th2 = ORD_INF;
+  if (T > PCAP) {  // thresholds: a quantile of 64 sampled rows / columns each
+    const int stride = TP / 64;
+    const int sr = min(63, max(0, (int)(want / (float)stride) - 1));
+    uint64_t x[2], y[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int col = (lane * 2 + i) * stride;
+      x[i] = col < T ? ((uint64_t)f2ord(d2[col]) << 32) : ~0ull;
+      y[i] = col < T ? ((uint64_t)f2ord(d1[col]) << 32) : ~0ull;
+    }
+    warp_sort<2>(x);
+    warp_sort<2>(y);
+    th2 = (uint32_t)(__shfl_sync(0xffffffffu, x[sr & 1], sr >> 1) >> 32);
+    th1 = (uint32_t)(__shfl_sync(0xffffffffu, y[sr & 1], sr >> 1) >> 32);
+  }
+  int P2 = 0, R = 0;
+  for (int t0 = 0; t0 < T; t0 += 8 * 32) {
+    // eight loads in flight per lane before the compaction uses them
+    uint32_t kc[8];
+    float dr[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u * 32 + lane;
+      kc[u] = t < T ? f2ord(__ldg(d2 + t)) : ORD_INF;
+      dr[u] = t < T ? __ldg(d1 + t) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u * 32 + lane;
+      const bool tc = t < T && kc[u] <= th2;
+      const bool tr = t < T && f2ord(dr[u]) <= th1;
+      const uint32_t mc = __ballot_sync(0xffffffffu, tc);
+      const uint32_t mr = __ballot_sync(0xffffffffu, tr);
+      const int pc = P2 + __popc(mc & lanemask_lt());
+      const int pr = R + __popc(mr & lanemask_lt());
+      if (tc && pc < PCAP) W.band[pc] = ((uint64_t)kc[u] << 32) | (uint32_t)t;
+      if (tr && pr < RCAP) {
+        W.rs1[pr] = dr[u];
+        W.rid[pr] = (uint16_t)t;
+      }
+      P2 += __popc(mc);
+      R += __popc(mr);
+    }
+  }
+  if (P2 > PCAP || R > RCAP) return false;
+  __syncwarp();
+  warp_sort_buf(W.band, P2);
+  __syncwarp();
+  for (int v = lane; v < P2; v += 32) {
+    const uint64_t e = W.band[v];
+    W.cs2[v] = ord2f((uint32_t)(e >> 32));
+    W.cp2[v] = (uint16_t)(uint32_t)e;
+  }
+  __syncwarp();
+  for (int r = lane; r < R; r += 32) {
+    const int v = W.vloid[W.rid[r]];
+    W.rfk[r] = v < P2 ? f2ord(__fadd_rn(W.rs1[r], W.cs2[v])) : ORD_INF;
+  }
+  __syncwarp();
+  *P2out = P2;
+  *Rout = R;
+  *limit = (th2 == ORD_INF) ? ORD_INF
+                            : min(f2ord(__fadd_rn(min1, ord2f(th2))), f2ord(__fadd_rn(ord2f(th1), min2)));
+  return true;
+}
+
 __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs a) {
   __shared__ WarpSmem smw[WPB];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -813,79 +888,26 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
     const int64_t L = a.L ? (int64_t)a.L[q] : (int64_t)a.L_scalar;
     const float* d1 = a.d1 + q * T;
     const float* d2 = a.d2 + q * T;
+    // rows and columns for about 5 sqrt(L / rho) + 32 visited cells; a query
+    // that would need more than the caps goes straight to the CTA kernel
+    float want = 5.f * sqrtf((float)L / rho) + 32.f;
+    const float want_max = 0.9f * (float)PCAP;
+    if (want > want_max && T > PCAP) {
+      if (lane == 0) a.ncells[q] = FALLBACK;
+      continue;
+    }
     __syncwarp();
-    // minima of both lists
     uint32_t m1 = ORD_INF, m2 = ORD_INF;
+#pragma unroll 8
     for (int t = lane; t < T; t += 32) {
-      m1 = min(m1, f2ord(d1[t]));
-      m2 = min(m2, f2ord(d2[t]));
+      m1 = min(m1, f2ord(__ldg(d1 + t)));
+      m2 = min(m2, f2ord(__ldg(d2 + t)));
+      W.vloid[t] = 0;
     }
     const float min1 = ord2f(warp_min_u32(m1)), min2 = ord2f(warp_min_u32(m2));
-    // column threshold from a sample of 256 columns
-    uint32_t th2 = ORD_INF;
-    if (T > PCAP) {
-      const int stride = TP / 256;
-      uint64_t x[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int col = (lane * 8 + i) * stride;
-        x[i] = col < T ? ((uint64_t)f2ord(d2[col]) << 32) : ~0ull;
-      }
-      warp_sort<8>(x);
-      // about 2 sqrt(L / rho) columns, at most half the prefix capacity
-      const float want = fminf((float)PCAP * 0.5f, fmaxf(32.f, 2.f * sqrtf((float)L / rho)));
-      const int sr = min(255, max(0, (int)(want / (float)stride) - 1));
-      th2 = (uint32_t)(__shfl_sync(0xffffffffu, x[sr & 7], sr >> 3) >> 32);
-    }
-    bool fb = false;
-    // compact the columns with d2 <= theta2
-    int P2 = 0;
-    for (int t0 = 0; t0 < T; t0 += 32) {
-      const int t = t0 + lane;
-      const uint32_t key = t < T ? f2ord(d2[t]) : ORD_INF;
-      const bool take = t < T && key <= th2;
-      const uint32_t m = __ballot_sync(0xffffffffu, take);
-      const int pos = P2 + __popc(m & lanemask_lt());
-      if (take && pos < PCAP) W.band[pos] = ((uint64_t)key << 32) | (uint32_t)t;
-      P2 += __popc(m);
-    }
-    if (P2 > PCAP) fb = true;
-    // rows with d1 <= theta1 = min1 + theta2 - min2
-    uint32_t limit = ORD_INF, th1 = ORD_INF;
-    if (th2 != ORD_INF) {
-      const float th2f = ord2f(th2);
-      const float th1f = min1 + (th2f - min2);
-      th1 = f2ord(th1f);
-      limit = min(f2ord(__fadd_rn(min1, th2f)), f2ord(__fadd_rn(th1f, min2)));
-    }
-    int R = 0;
-    for (int t0 = 0; t0 < T; t0 += 32) {
-      const int t = t0 + lane;
-      const float dv = t < T ? d1[t] : 0.f;
-      const bool take = t < T && f2ord(dv) <= th1;
-      const uint32_t m = __ballot_sync(0xffffffffu, take);
-      const int pos = R + __popc(m & lanemask_lt());
-      if (take && pos < RCAP) {
-        W.rs1[pos] = dv;
-        W.rid[pos] = (uint16_t)t;
-        W.rvlo[pos] = 0;
-      }
-      R += __popc(m);
-    }
-    if (R > RCAP) fb = true;
-    __syncwarp();
-    if (!fb) {
-      warp_sort_buf(W.band, P2);
-      __syncwarp();
-      for (int v = lane; v < P2; v += 32) {
-        const uint64_t e = W.band[v];
-        W.cs2[v] = ord2f((uint32_t)(e >> 32));
-        W.cp2[v] = (uint16_t)(uint32_t)e;
-      }
-      __syncwarp();
-      for (int r = lane; r < R; r += 32) W.rfk[r] = f2ord(__fadd_rn(W.rs1[r], W.cs2[0]));
-      __syncwarp();
-    }
+    int P2 = 0, R = 0;
+    uint32_t limit = ORD_INF;
+    bool fb = !build_grid(W, d1, d2, T, TP, want, min1, min2, &P2, &R, &limit);
     long long committed = 0;
     int nout = 0;
     bool overflow = false;
@@ -900,15 +922,22 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
       fm = warp_min_u64(fm);
       const uint32_t hmin = (uint32_t)(fm >> 32);
       if (fm == ~0ull || hmin >= limit) {
-        if (limit != ORD_INF) fb = true;  // the grid is used up before the budget
-        break;                            // else: every cell visited
+        if (limit == ORD_INF) break;  // every cell visited
+        // the grid is used up before the budget: a larger one, or the CTA kernel
+        if (want >= want_max) {
+          fb = true;
+          break;
+        }
+        want = fminf(want_max, 2.f * want);
+        fb = !build_grid(W, d1, d2, T, TP, want, min1, min2, &P2, &R, &limit);
+        continue;
       }
       const int rh = (int)(uint32_t)fm;
       auto count = [&](uint32_t h) -> long long {
         long long c = 0;
         for (int r = lane; r < R; r += 32) {
           if (W.rfk[r] <= h) {
-            const int v = W.rvlo[r];
+            const int v = W.vloid[W.rid[r]];
             c += row_count(W.cs2, P2, W.rs1[r], v + 1, h) - v;
           }
         }
@@ -920,7 +949,7 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
         break;
       }
       const uint32_t lim1 = limit == ORD_INF ? ORD_INF - 1 : limit - 1;
-      const int vh = W.rvlo[rh];
+      const int vh = W.vloid[W.rid[rh]];
       const float sh = W.rs1[rh];
       const uint32_t g_hi = min(lim1, f2ord(__fadd_rn(sh, W.cs2[min(P2 - 1, vh + BCAP)])));
       const uint32_t g1 = min(g_hi, f2ord(__fadd_rn(sh, W.cs2[min(P2 - 1, vh + 16)])));
@@ -968,10 +997,10 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
         }
       }
       const uint32_t h = lo;
-      // the band's cells: columns [rvlo, rvhi) of every row
+      // the band's cells: columns [vlo, vhi) of every row
       int loc = 0;
       for (int r = lane; r < R; r += 32) {
-        const int v = W.rvlo[r];
+        const int v = W.vloid[W.rid[r]];
         const int vhi = (W.rfk[r] <= h) ? row_count(W.cs2, P2, W.rs1[r], v + 1, h) : v;
         W.rvhi[r] = (uint16_t)vhi;
         loc += vhi - v;
@@ -979,39 +1008,51 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
       int E;
       int pos = warp_excl_scan(loc, &E);
       for (int r = lane; r < R; r += 32) {
-        const int v0 = W.rvlo[r], v1 = W.rvhi[r];
+        const int v0 = W.vloid[W.rid[r]], v1 = W.rvhi[r];
         const uint32_t rowbase = (uint32_t)W.rid[r] * (uint32_t)T;
         const float s1r = W.rs1[r];
         for (int v = v0; v < v1; ++v)
           W.band[pos++] = ((uint64_t)f2ord(__fadd_rn(s1r, W.cs2[v])) << 32) | (rowbase + W.cp2[v]);
       }
       __syncwarp();
-      // sort the band by (key, cell id); lane l holds entries 8l .. 8l + 7
+      // lane l holds entries 8l .. 8l + 7
       uint64_t x[8];
+      uint32_t cnt[8], beg[8];
+      long long mysum = 0;
+      auto load_counts = [&]() {
+        mysum = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          cnt[i] = 0;
+          beg[i] = 0;
+          if (lane * 8 + i < E) {
+            const uint32_t cell = (uint32_t)x[i];
+            beg[i] = __ldg(a.offsets + cell);
+            cnt[i] = __ldg(a.offsets + cell + 1) - beg[i];
+          }
+          mysum += cnt[i];
+        }
+      };
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int e = lane * 8 + i;
         x[i] = e < E ? W.band[e] : ~0ull;
       }
-      warp_sort<8>(x);
-      uint32_t cnt[8], beg[8];
-      long long mysum = 0;
-      int mynz = 0;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        cnt[i] = 0;
-        beg[i] = 0;
-        if (lane * 8 + i < E) {
-          const uint32_t cell = (uint32_t)x[i];
-          beg[i] = a.offsets[cell];
-          cnt[i] = a.offsets[cell + 1] - beg[i];
-        }
-        mysum += cnt[i];
-        mynz += cnt[i] > 0;
-      }
-      long long band_pts;
-      long long before = warp_excl_scan(mysum, &band_pts);
       const long long need = L - committed;
+      bool sorted = false;
+      if (a.ordered) {
+        warp_sort<8>(x);
+        sorted = true;
+      }
+      load_counts();
+      long long band_pts = warp_sum(mysum);
+      if (!sorted && band_pts >= need) {
+        // the last band: its cut needs the (key, cell id) order
+        warp_sort<8>(x);
+        load_counts();
+      }
+      long long dummy;
+      const long long before = warp_excl_scan(mysum, &dummy);
       // the cut: first entry whose running count reaches need
       int cut = E;  // entries [0, cut) are emitted
       {
@@ -1026,7 +1067,8 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
         if (first != (1 << 30)) cut = first + 1;
       }
       // emit the non-empty entries before the cut, in order
-      int nzb = 0, nz_total;
+      int nz_total;
+      int nzb;
       {
         int mine = 0;
 #pragma unroll
@@ -1053,9 +1095,10 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
       committed += emitted_pts;
       if (band_pts >= need) break;
       // next band: advance every row to its band end
+      __syncwarp();
       for (int r = lane; r < R; r += 32) {
         const int v = W.rvhi[r];
-        W.rvlo[r] = (uint16_t)v;
+        W.vloid[W.rid[r]] = (uint16_t)v;
         W.rfk[r] = v < P2 ? f2ord(__fadd_rn(W.rs1[r], W.cs2[v])) : ORD_INF;
       }
       __syncwarp();
@@ -1081,12 +1124,17 @@ void launch_traverse(const TraverseArgs& a, cudaStream_t st) {
   BPQ_CHECK(a.T >= 1 && a.T <= MAX_T, BPQ_EINVAL, "T out of range for the traversal");
   const size_t smem = smem_layout(a.T).total;
   BPQ_CHECK(smem <= 227 * 1024, BPQ_EINVAL, "T too large for the traversal's shared memory");
-  // common path: one warp per query
+  BPQ_CUDA(cudaFuncSetAttribute(traverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (a.T > WARP_TMAX) {  // the general path for every query
+    const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
+    traverse_kernel<<<grid, NT, smem, st>>>(a, 0);
+    check_launch("traverse kernel");
+    return;
+  }
+  // common path: one warp per query; then the queries it marked, one CTA each
   const int wgrid = (int)std::min<int64_t>((a.nq + WPB - 1) / WPB, 1 << 20);
   traverse_warp_kernel<<<wgrid, WPB * 32, 0, st>>>(a);
   check_launch("traverse warp kernel");
-  // queries the warp kernel marked: one CTA per query
-  BPQ_CUDA(cudaFuncSetAttribute(traverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = (int)std::min<int64_t>(a.nq, 4096);
   traverse_kernel<<<grid, NT, smem, st>>>(a, 1);
   check_launch("traverse kernel");
