@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--n-query", type=int, default=None, help="override the queries per step (profiling only)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the L / scorer sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the Poisson serving measurement")
+    ap.add_argument("--serve-seconds", type=float, default=0.25, help="arrival window per offered load")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -417,6 +419,8 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_sweep:
         out["sweep"] = sweep(ix, queries, w, k, flush, stream)
         out["recall"] = recall(ix, queries, w, mix, L, k, dev)
+    if rank == 0 and world == 1 and not args.no_serve:
+        out["serve"] = serve_block(ix, w, mix, k, args.serve_seconds)
 
     if world > 1:
         dist.barrier()
@@ -431,6 +435,29 @@ def run_ours(args):
                                "oracle_index_build_s": round(res["build_s"], 1)}
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def serve_block(ix, w, mix, k, seconds, seed=11, n_max=300_000, max_batch=4096):
+    """Poisson stream with per-query L uniform over {1k, 10k, 100k}: latency p50 / p99 at 50 % and 80 %
+    of the saturated throughput of the same mix (full batches through the same host-buffer call)."""
+    import numpy as np
+
+    import synthdata as sd
+    from paper_1404_1831_gb300 import serving
+    from synthdata import device as sdev
+    qh = sdev.points_cuda(mix, sd.STREAM_QUERY, w.n_query, n_max).cpu().numpy()  # after the timed batch
+    mix_L = np.array([1_000, 10_000, 100_000], dtype=np.int64)
+    Ls = mix_L[np.random.default_rng(seed).integers(0, len(mix_L), n_max)]
+    sat = serving.saturated_qps(ix, qh, Ls, k, batch=max_batch)
+    out = {"L_mix": mix_L.tolist(), "k": k, "max_batch": max_batch, "saturated_qps": sat,
+           "latency": "arrival to results in host memory (bpq_search_host: H2D, search, D2H)", "loads": {}}
+    for load in (0.5, 0.8):
+        rate = load * sat
+        n = int(min(n_max, max(1000, rate * seconds)))
+        res = serving.serve(ix, qh[:n], Ls[:n], serving.poisson_arrivals(n, rate, seed + int(10 * load)), k,
+                            max_batch=max_batch)
+        out["loads"][f"{load:.1f}"] = {"offered_qps": rate, **res.summary()}
+    return out
 
 
 def sweep(ix, queries, w, k, flush, stream, steps=3):

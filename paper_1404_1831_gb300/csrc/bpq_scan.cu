@@ -315,6 +315,7 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
       thr = EMPTY;
       nbuf = 0;
     }
+    __syncthreads();  // every thread reads nbuf / thr, also when the query has no cells
     const int nc = max(0, a.ncells[q]);
     const bpq_cell* cl = a.cells + q * (int64_t)a.cap;
     for (int cs = 0; cs < nc; cs += CH) {

@@ -1,0 +1,95 @@
+"""Parity at the full 10M-point workload (T = 1024, M = 8), on sampled queries.
+
+The oracle trains the codebooks (4 Lloyd iterations on 100k learn points) and
+encodes all 10M points in a pool of spawned processes; the GPU index is created
+from those codebooks and fed the same points from the device generator.  The
+lists must then agree bit for bit, and the GPU's answers for a 10k-query batch
+(the launch the benchmark times) must equal the oracle's on sampled queries at
+L = 1k, 10k and 100k.
+"""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+from tests.parity import assert_topk_match
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+LEARN, ITERS, CHUNK = 100_000, 4, 250_000
+SAMPLE = (0, 1, 2, 3, 1234, 4321, 7777, 9999)
+
+
+def _encode_chunk(task):
+    import synthdata as sd
+    from oracle import bpq_oracle as O
+    seed, n_comp, start, count, cb = task
+    x = sd.points(sd.make_mixture(seed, n_comp), sd.STREAM_BASE, start, count)
+    return O.encode_multi_d_adc(x, cb)
+
+
+@pytest.fixture(scope="module")
+def full():
+    import torch
+
+    import paper_1404_1831_gb300 as bpq
+    import synthdata as sd
+    from oracle import bpq_oracle as O
+    from synthdata import device as sdev
+    w = sd.SIFT10M
+    mix = sd.make_mixture(w.seed, w.n_comp)
+    cb = O.train_multi_d_adc(sd.points(mix, sd.STREAM_LEARN, 0, LEARN), w.T, w.M, ITERS)
+    tasks = [(w.seed, w.n_comp, s, min(CHUNK, w.n_base - s), cb) for s in range(0, w.n_base, CHUNK)]
+    saved = {v: os.environ.get(v) for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS")}
+    os.environ.update({v: "1" for v in saved})
+    try:
+        with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+            parts = pool.map(_encode_chunk, tasks)
+    finally:
+        for v, val in saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
+    cells = np.concatenate([p[0] for p in parts])
+    codes = np.concatenate([p[1] for p in parts])
+    index = O.OracleIndex(cb=cb, lists=O.build_lists(cells, codes, np.arange(w.n_base), w.T), variant="global",
+                          tables=O.fbpq_tables(cb))
+    ix = bpq.Index.create(cb.C1, cb.C2, cb.R)
+    for s in range(0, w.n_base, 2_000_000):
+        ix.add(sdev.points_cuda(mix, sd.STREAM_BASE, s, min(2_000_000, w.n_base - s)))
+    ix.finalize()
+    q = sdev.points_cuda(mix, sd.STREAM_QUERY, 0, w.n_query)
+    torch.cuda.synchronize()
+    return dict(w=w, mix=mix, index=index, ix=ix, q=q, qh=sd.points(mix, sd.STREAM_QUERY, 0, max(SAMPLE) + 1))
+
+
+def test_full_lists_bit_exact(full):
+    a = full["ix"].arrays()
+    lists = full["index"].lists
+    assert np.array_equal(a["offsets"].cpu().numpy().astype(np.int64), lists.offsets)
+    assert np.array_equal(a["codes"].cpu().numpy(), lists.codes)
+    assert np.array_equal(a["ids"].cpu().numpy().astype(np.int64), lists.ids)
+
+
+@pytest.mark.parametrize("L", [1_000, 10_000, 100_000])
+def test_full_search_sampled(full, L):
+    from oracle import bpq_oracle as O
+    k = 100
+    ids, dists = full["ix"].search(full["q"], L, k, "fbpq")
+    full["ix"].search_status()
+    ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+    exact = 0
+    for n in SAMPLE:
+        o_ids, o_d, _, _ = O.search_one(full["index"], full["qh"][n], L, k, "fbpq", traversal="full_sort")
+        exact += assert_topk_match(ids[n:n + 1], dists[n:n + 1], o_ids[None], o_d[None])
+    assert exact == len(SAMPLE)  # integer data: FP32 sums are exact
+
+
+def test_full_reconstruction_and_table_scorers_agree(full):
+    """The three scorers return the same lists at the benchmark's size (Eq. 8 vs Eq. 9)."""
+    a = [t.cpu().numpy() for t in full["ix"].search(full["q"], 10_000, 100, "fbpq")]
+    for scorer in ("fbpq_tables", "recon"):
+        b = [t.cpu().numpy() for t in full["ix"].search(full["q"], 10_000, 100, scorer)]
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])

@@ -242,3 +242,19 @@ def test_save_load_roundtrip_and_corruption(gpu, tmp_path):
     with pytest.raises(bpq.BpqError) as e:
         bpq.Index.load(bad)
     assert e.value.code == -4
+
+
+def test_serving_answers_equal_batch_search(gpu, tiny_oracle):
+    """The Poisson serving loop (dynamic batches through bpq_search_host) returns the
+    same lists as one batch search with the same per-query budgets."""
+    from paper_1404_1831_gb300 import serving
+    q = tiny_oracle["queries"].astype(np.float32)
+    n = len(q)
+    L = np.resize(np.array([1_000, 10_000, 3_000], dtype=np.int64), n)
+    res = serving.serve(gpu["ix"], q, L, serving.poisson_arrivals(n, 20_000.0, 5), k=50, max_batch=16)
+    ids, dists = gpu["ix"].search(gpu["q"], L, 50)
+    assert np.array_equal(res.ids, ids.cpu().numpy()) and np.array_equal(res.dists, dists.cpu().numpy())
+    assert res.batch_sizes.sum() == n and res.batch_sizes.max() <= 16
+    assert (res.latency_s > 0).all()
+    s = res.summary()
+    assert s["p50_ms"] <= s["p99_ms"] <= s["max_ms"]
