@@ -51,6 +51,9 @@ def parse_args():
     ap.add_argument("--no-sweep", action="store_true", help="skip the L / scorer sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the Poisson serving measurement")
+    ap.add_argument("--workload", choices=("sift10m", "c3", "c4", "c5"), default="sift10m",
+                    help="c3: 100M, M=16, int8 shortlist; c4: 100M, local codebooks, uneven L; "
+                         "c5: 1B points, serving (each prints its own JSON line)")
     ap.add_argument("--serve-seconds", type=float, default=0.25, help="arrival window per offered load")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -485,6 +488,121 @@ def sweep(ix, queries, w, k, flush, stream, steps=3):
     return res
 
 
+def exact_nn_gpu(q, w, mix, dev, chunk=2_000_000):
+    """Exact nearest neighbour of each query over the base points, by brute force in
+    FP32 with TF32 off (integer data: every partial sum is an integer below 2^24)."""
+    import torch
+
+    import synthdata as sd
+    from synthdata import device as sdev
+    n = q.shape[0]
+    qn = (q * q).sum(1, keepdim=True)
+    best = torch.full((n,), float("inf"), device=dev)
+    arg = torch.zeros(n, dtype=torch.int64, device=dev)
+    for s in range(0, w.n_base, chunk):
+        x = sdev.points_cuda(mix, sd.STREAM_BASE, s, min(chunk, w.n_base - s), device=dev)
+        d = qn - 2.0 * (q @ x.T) + (x * x).sum(1)[None, :]
+        m, a = d.min(1)
+        upd = m < best
+        best = torch.where(upd, m, best)
+        arg = torch.where(upd, a + s, arg)
+    return arg
+
+
+def recall_of(ids, nn):
+    hit = (ids.long() == nn[:, None])
+    return {f"R@{R}": float(hit[:, :R].any(1).float().mean()) for R in (1, 10, 100)}
+
+
+def run_config(args):
+    """The larger configurations: C3 (100M, M = 16: FP32 FBPQ vs the int8 shortlist with
+    exact re-scoring at L = 30k), C4 (100M, local codebooks, L = round(10^U(3, 5)) per
+    query: HBPQ vs the global codebooks' FBPQ and reconstruction), C5 (1B points:
+    batch queries/s per L and Poisson serving latency)."""
+    import numpy as np
+    import torch
+
+    import paper_1404_1831_gb300 as bpq
+    import synthdata as sd
+    from synthdata import device as sdev
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    w = {"c3": sd.SIFT100M_M16, "c4": sd.SIFT100M, "c5": sd.SIFT1B}[args.workload]
+    mix = sd.make_mixture(w.seed, w.n_comp)
+    learn = sdev.points_cuda(mix, sd.STREAM_LEARN, 0, w.n_learn, device=dev)
+
+    def build(variant):
+        t0 = time.time()
+        ix = bpq.Index.train(learn, w.T, w.M, variant=variant, iters=w.kmeans_iters)
+        for s in range(0, w.n_base, 4_000_000):
+            ix.add(sdev.points_cuda(mix, sd.STREAM_BASE, s, min(4_000_000, w.n_base - s), device=dev))
+        ix.finalize()
+        torch.cuda.synchronize()
+        return ix, time.time() - t0
+
+    q = sdev.points_cuda(mix, sd.STREAM_QUERY, 0, w.n_query, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=5, warm=3):
+        ts = []
+        for r in range(warm + reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r >= warm:
+                ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    k, nq = 100, w.n_query
+    out = {"workload": w.name, "n_base": w.n_base, "T": w.T, "M": w.M, "n_query": nq, "k": k, "dtype": "f32",
+           "data": "synthetic", "l2": "flushed between timed runs (512 MB write)", "timing": "median of 5 after 3 warm-up"}
+    if args.workload == "c3":
+        L, S = 30_000, 1000
+        ix, out["build_s"] = build("global")
+        ms32 = timed(lambda: ix.search(q, L, k, "fbpq"))
+        ms8 = timed(lambda: ix.search_shortlist(q, L, k, shortlist=S))
+        a_ids, a_d = ix.search(q, L, k, "fbpq")
+        b_ids, b_d = ix.search_shortlist(q, L, k, shortlist=S)
+        A, B = a_ids.cpu().numpy(), b_ids.cpu().numpy()
+        overlap = np.mean([len(np.intersect1d(A[n], B[n])) / k for n in range(nq)])
+        nn = exact_nn_gpu(q[:1000], w, mix, dev)
+        out.update({"L": L, "shortlist": S, "lut": "int8, per-query step, offsets per sub-quantizer",
+                    "fbpq_f32": {"qps": nq / (ms32 / 1e3), "ms": ms32, "recall": recall_of(a_ids[:1000], nn)},
+                    "shortlist_i8": {"qps": nq / (ms8 / 1e3), "ms": ms8, "recall": recall_of(b_ids[:1000], nn)},
+                    "identical_lists": float((a_ids == b_ids).all(1).float().mean()),
+                    "mean_top100_overlap": float(overlap),
+                    "max_abs_dist_diff_same_rank": float((a_d - b_d).abs()[(a_ids == b_ids)].max())})
+    elif args.workload == "c4":
+        Ls = np.round(10.0 ** np.random.default_rng(7).uniform(3.0, 5.0, nq)).astype(np.int64)
+        out.update({"L": "round(10^U(3,5)) per query, seed 7", "L_mean": float(Ls.mean())})
+        nn = exact_nn_gpu(q[:1000], w, mix, dev)
+        ixl, out["build_local_s"] = build("local")
+        ms = timed(lambda: ixl.search(q, Ls, k, "hbpq"))
+        ids, _ = ixl.search(q, Ls, k, "hbpq")
+        out["hbpq"] = {"qps": nq / (ms / 1e3), "ms": ms, "recall": recall_of(ids[:1000], nn)}
+        del ixl
+        ixg, out["build_global_s"] = build("global")
+        for scorer in ("fbpq", "recon"):
+            ms = timed(lambda: ixg.search(q, Ls, k, scorer))
+            ids, _ = ixg.search(q, Ls, k, scorer)
+            out[scorer] = {"qps": nq / (ms / 1e3), "ms": ms, "recall": recall_of(ids[:1000], nn)}
+    else:
+        ix, out["build_s"] = build("global")
+        out["batch"] = {}
+        for L in w.L:
+            ms = timed(lambda: ix.search(q, L, k, "fbpq"))
+            out["batch"][f"L{L}"] = {"qps": nq / (ms / 1e3), "ms": ms}
+        out["serve"] = serve_block(ix, w, mix, k, args.serve_seconds)
+    out["index"] = {"device_bytes": int(ix.info().device_bytes) if args.workload != "c4" else int(ixg.info().device_bytes)}
+    print(json.dumps(out), flush=True)
+
+
 def recall(ix, queries, w, mix, L, k, dev, n_gt=1000):
     """Recall@1/10/100 of the search against exact nearest neighbours (brute force
     in FP32 with TF32 off: every partial sum is an integer below 2^24, so exact)."""
@@ -543,6 +661,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "sift10m":
+        run_config(args)
     else:
         run_ours(args)
 

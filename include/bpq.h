@@ -219,6 +219,30 @@ int bpq_search(const bpq_index* idx, const float* queries_dev, int64_t nq, const
                void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /*
+ * bpq_search_shortlist — FBPQ search with a reduced-precision table and exact
+ * re-scoring (a precision variant of §3.1; the paper scans with full-precision
+ * tables).  Per query:
+ *  1. the PQ table lut[k][t] of Eq. 8/9 is shifted per sub-quantizer by its
+ *     minimum lo_k and quantized with one per-query step s = max_k(max_t lut[k][t]
+ *     - lo_k) / 255 (FP32 division; s = 1 if every table is constant):
+ *     q8[k][t] = round_half_even((lut[k][t] - lo_k) / s), an integer in [0, 255];
+ *  2. every candidate of the visited cells (the same cells as bpq_search) gets the
+ *     score (key(i,j) + cross(p)) + s * sum_k q8[k][c_k] in FP32, in that order
+ *     (the constant sum_k lo_k is left out), and the `shortlist` best by (score,
+ *     position in the index lists) are kept;
+ *  3. those are re-scored with the exact FBPQ distance (Eq. 8-9, as bpq_search)
+ *     and the k best by (distance, id) are returned as by bpq_search.
+ *  lut_precision: BPQ_LUT_I8 (the only one); shortlist in [k, 1024].
+ *  Needs the global variant.  workspace: bpq_search_shortlist_workspace_size
+ *  bytes or fewer (chunks, as bpq_search).  Asynchronous on stream.
+ */
+enum { BPQ_LUT_I8 = 1 };
+size_t bpq_search_shortlist_workspace_size(const bpq_index* idx, int64_t nq, int64_t L_max, int32_t shortlist);
+int bpq_search_shortlist(const bpq_index* idx, const float* queries_dev, int64_t nq, const int64_t* L_host,
+                         int64_t L_stride, int32_t k, int32_t shortlist, int32_t lut_precision, int32_t* ids_dev,
+                         float* dists_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/*
  * bpq_scan — the scan and top-k stage of bpq_search alone (§2.3.3 reranking,
  * §3.1, §3.2), on cells written by bpq_traverse: for each query the k smallest
  * (distance, id) over every point of its ncells_dev[q] visited cells.

@@ -399,6 +399,84 @@ def dist_fbpq(q, cb: Codebooks, tab: FbpqTables, cell, codes):
 
 
 # ----------------------------------------------------------------------------
+# Reduced-precision table with exact re-scoring (a precision variant of §3.1;
+# the paper's own scan uses full-precision tables).  The score is formed in
+# IEEE FP32 in a fixed order so that a GPU computing it the same way agrees bit
+# for bit; everything else stays FP64.
+# ----------------------------------------------------------------------------
+
+
+def pq_table(q, cb: Codebooks):
+    """Per-query PQ table of §3.1: lut[k][t] = ||R_k[t]||^2 - 2<q_k, R_k[t]>, the
+    query term of Eq. 8 plus the codeword norm of Eq. 9, shape (M, 256)."""
+    q = np.asarray(q, np.float64)
+    s = cb.sub
+    R = cb.R.astype(np.float64)
+    return np.stack([(R[k] * R[k]).sum(1) - 2.0 * (R[k] @ q[k * s:(k + 1) * s]) for k in range(cb.M)])
+
+
+def point_cross(cb: Codebooks, tab: FbpqTables, cell, codes):
+    """The query-independent cross terms of Eq. 9 for each point:
+    2 sum_{k<=M/2} <c^1_i, r_k> + 2 sum_{k>M/2} <c^2_j, r_k>."""
+    cell = np.asarray(cell, dtype=np.int64)
+    codes = np.asarray(codes, dtype=np.int64)
+    m2 = cb.M // 2
+    i, j = cell // cb.T, cell % cb.T
+    return 2.0 * (sum(tab.X1[i, k, codes[:, k]] for k in range(m2))
+                  + sum(tab.X2[j, k, codes[:, m2 + k]] for k in range(m2)))
+
+
+def quantize_table_int8(lut):
+    """Per sub-quantizer offset lo_k = min_t lut[k][t] and one per-query step
+    s = max_k (max_t lut[k][t] - lo_k) / 255 (1 when every table is constant);
+    q8[k][t] = round_half_even((lut[k][t] - lo_k) / s) in [0, 255].  The table
+    entries are integers below 2^24 (integer grid), so their FP32 copies are exact
+    and only the division rounds.  Returns (q8 int64 (M, 256), s float32)."""
+    lut32 = np.asarray(lut, np.float64).astype(np.float32)
+    x = lut32 - lut32.min(axis=1)[:, None]
+    rng = x.max()
+    step = np.float32(rng) / np.float32(255.0) if rng > 0 else np.float32(1.0)
+    q8 = np.clip(np.rint(x / step), 0, 255).astype(np.int64)
+    return q8, np.float32(step)
+
+
+def search_shortlist_one(index: OracleIndex, q, L, k, S):
+    """One query of the int8-table search: the visited cells and candidates of
+    search_one; score = (key(i,j) + cross(p)) + s * sum_k q8[k][c_k] in FP32 (the
+    constant sum_k lo_k is left out); the S best by (score, list position) are
+    re-scored with the exact FBPQ distance (Eqs. 8-9) and ranked by (distance, id).
+    Returns (ids (k,), dists (k,))."""
+    cb, lists, tab = index.cb, index.lists, index.tables
+    if index.variant != "global":
+        raise ValueError("the int8 shortlist scores global codes")
+    d1, d2 = coarse_distances(q, cb)
+    cells, _, _ = traverse_full_sort(d1, d2, lists.counts(), L)
+    pos = candidates(cells, lists)
+    cell_of = np.repeat(cells, lists.counts()[cells])
+    codes = lists.codes[pos].astype(np.int64)
+    i, j = cell_of // cb.T, cell_of % cb.T
+    key32 = (d1[i] + d2[j]).astype(np.float32)
+    cross32 = point_cross(cb, tab, cell_of, codes).astype(np.float32)
+    q8, step = quantize_table_int8(pq_table(q, cb))
+    isum = q8[np.arange(cb.M)[None, :], codes].sum(1).astype(np.float32)
+    score = (key32 + cross32) + step * isum
+    short = np.lexsort((pos, score))[:S]
+    exact = dist_fbpq(q, cb, tab, cell_of[short], codes[short])
+    return topk(exact, lists.ids[pos[short]], k)
+
+
+def search_shortlist(index: OracleIndex, queries, L, k, S):
+    queries = np.asarray(queries)
+    nq = len(queries)
+    Ls = np.broadcast_to(np.asarray(L, dtype=np.int64), (nq,))
+    ids = np.empty((nq, k), dtype=np.int64)
+    dists = np.empty((nq, k))
+    for n in range(nq):
+        ids[n], dists[n] = search_shortlist_one(index, queries[n], int(Ls[n]), k, S)
+    return ids, dists
+
+
+# ----------------------------------------------------------------------------
 # Ranking, search, ground truth and recall
 # ----------------------------------------------------------------------------
 

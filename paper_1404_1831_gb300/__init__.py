@@ -19,6 +19,7 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "EIO", -4: "ECORRUPT", -5: "ETIMEOUT",
           -8: "ESTATE"}
 VARIANT_GLOBAL, VARIANT_LOCAL = 0, 1
 SCORERS = {"fbpq": 0, "recon": 1, "hbpq": 2, "fbpq_tables": 3}
+LUT_PRECISIONS = {"int8": 1}
 
 
 class BpqError(RuntimeError):
@@ -62,6 +63,9 @@ _SIGS = {
     "bpq_search": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P,
                                   _P, _P, ctypes.c_size_t, _P]),
     "bpq_search_status": (ctypes.c_int, [_P, _P, _P]),
+    "bpq_search_shortlist_workspace_size": (ctypes.c_size_t, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32]),
+    "bpq_search_shortlist": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_size_t, _P]),
     "bpq_scan": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                 _P, _P, _P, _P]),
     "bpq_search_host": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
@@ -301,6 +305,23 @@ class Index:
             self._counter = torch.zeros(1, dtype=torch.int32, device=cells.device)
         _check(lib().bpq_scan(self._h, _ptr(q), nq, _ptr(lut), _ptr(cells), _ptr(ncells), cap, k, SCORERS[scorer],
                               _ptr(ids), _ptr(dists), _ptr(self._counter), _stream(stream)))
+        return ids, dists
+
+    def search_shortlist(self, q, L, k, shortlist=1000, precision="int8", stream=None, workspace=None):
+        """bpq_search_shortlist: int8-table scan to a shortlist, exact FBPQ re-score, top k."""
+        import torch
+        nq = q.shape[0]
+        Ls, stride = _L_array(L, nq)
+        ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=q.device)
+        if workspace is None:
+            need = lib().bpq_search_shortlist_workspace_size(self._h, nq, int(Ls.max()), shortlist)
+            if self._ws is None or self._ws.numel() < need:
+                self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=torch.device("cuda", self.device))
+            workspace = self._ws
+        _check(lib().bpq_search_shortlist(self._h, _ptr(q), nq, Ls.ctypes.data, stride, k, shortlist,
+                                          LUT_PRECISIONS[precision], _ptr(ids), _ptr(dists), _ptr(workspace),
+                                          workspace.numel(), _stream(stream)))
         return ids, dists
 
     def search_noalloc(self, q, L, k, scorer="fbpq", stream=None, status=None):

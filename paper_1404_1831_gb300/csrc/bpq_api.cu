@@ -264,6 +264,111 @@ void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t*
 }
 
 // ---------------------------------------------------------------------------
+// bpq_search_shortlist: the bpq_search layout plus the int8 tables, their steps
+// and the shortlists.
+// ---------------------------------------------------------------------------
+struct ShortlistLayout {
+  Layout base;
+  size_t lut8, scale, sl, total;
+};
+
+ShortlistLayout shortlist_layout(const bpq_index& ix, int64_t nq, int64_t L_max, int S) {
+  ShortlistLayout l{};
+  l.base = layout(ix, nq, L_max, BPQ_SCORER_FBPQ, true);
+  size_t o = l.base.total;
+  l.lut8 = o;
+  o = align_up(o + (size_t)nq * ix.p.M * KSUB);
+  l.scale = o;
+  o = align_up(o + (size_t)nq * 4);
+  l.sl = o;
+  o = align_up(o + (size_t)nq * S * 8);
+  l.total = o;
+  return l;
+}
+
+void run_shortlist(const bpq_index& ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride, int k,
+                   int S, int32_t* out_ids, float* out_dists, void* ws, size_t ws_bytes, cudaStream_t st) {
+  std::vector<int32_t> Lq;
+  const int64_t L_max = read_L(L_host, L_stride, nq, &Lq);
+  BPQ_CHECK(k >= 1 && S >= k && S <= MAX_K, BPQ_EINVAL, "need 1 <= k <= shortlist <= 1024");
+  check_scorer(ix, BPQ_SCORER_FBPQ);
+  BPQ_CHECK(ix.p.D == 128 && (ix.p.M == 8 || ix.p.M == 16), BPQ_EINVAL,
+            "the int8 shortlist is built for D = 128, M = 8 or 16");
+  if (nq <= 0) return;
+  BPQ_CHECK(q && ws && out_ids && out_dists, BPQ_EINVAL, "NULL pointer");
+  int64_t chunk = nq;
+  if (shortlist_layout(ix, chunk, L_max, S).total > ws_bytes) {
+    int64_t lo = 0, hi = nq;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) / 2;
+      if (shortlist_layout(ix, mid, L_max, S).total <= ws_bytes) lo = mid; else hi = mid;
+    }
+    chunk = lo;
+  }
+  BPQ_CHECK(chunk >= 1, BPQ_ECAPACITY, "workspace too small for one query");
+  const ShortlistLayout l = shortlist_layout(ix, chunk, L_max, S);
+  char* w = static_cast<char*>(ws);
+  BPQ_CUDA(cudaMemsetAsync(w + l.base.status, 0, 4, st));
+  const float rho = (float)((double)ix.n_points / (double)std::max<int64_t>(1, ix.n_nonempty));
+  for (int64_t c0 = 0; c0 < nq; c0 += chunk) {
+    const int64_t nc = std::min(chunk, nq - c0);
+    const float* qc = q + c0 * ix.p.D;
+    float* d1 = reinterpret_cast<float*>(w + l.base.d1);
+    float* d2 = reinterpret_cast<float*>(w + l.base.d2);
+    float* lut = reinterpret_cast<float*>(w + l.base.lut);
+    uint8_t* lut8 = reinterpret_cast<uint8_t*>(w + l.lut8);
+    float* scale = reinterpret_cast<float*>(w + l.scale);
+    uint64_t* sl = reinterpret_cast<uint64_t*>(w + l.sl);
+    launch_query_tables(ix, qc, nc, d1, d2, lut, st);
+    launch_quant_lut(lut, ix.p.M, nc, lut8, scale, st);
+    TraverseArgs ta{};
+    ta.d1 = d1;
+    ta.d2 = d2;
+    ta.offsets = ix.offsets.as<uint32_t>();
+    if (L_stride) {
+      BPQ_CUDA(cudaMemcpyAsync(w + l.base.L, Lq.data() + c0, nc * 4, cudaMemcpyHostToDevice, st));
+      ta.L = reinterpret_cast<const int32_t*>(w + l.base.L);
+    } else {
+      ta.L = nullptr;
+      ta.L_scalar = (int32_t)L_host[0];
+    }
+    ta.T = ix.p.T;
+    ta.rho = rho;
+    ta.ordered = 0;
+    ta.status = reinterpret_cast<int32_t*>(w + l.base.status);
+    ta.nq = nc;
+    ta.cap = (int32_t)l.base.cap;
+    ta.cells = reinterpret_cast<bpq_cell*>(w + l.base.cells);
+    ta.ncells = reinterpret_cast<int32_t*>(w + l.base.ncells);
+    ta.npoints = reinterpret_cast<int64_t*>(w + l.base.npoints);
+    launch_traverse(ta, st);
+    ScanArgs sa = scan_args(ix, qc, nc, lut, ta.cells, ta.ncells, ta.cap, S, nullptr, nullptr,
+                            reinterpret_cast<int32_t*>(w + l.base.qcounter));
+    sa.lut8 = lut8;
+    sa.lut_scale = scale;
+    sa.sl_out = sl;
+    launch_scan_q8(sa, st);
+    RescoreArgs r{};
+    r.sl = sl;
+    r.S = S;
+    r.k = k;
+    r.T = ix.p.T;
+    r.M = ix.p.M;
+    r.nq = nc;
+    r.d1 = d1;
+    r.d2 = d2;
+    r.lut = lut;
+    r.offsets = ix.offsets.as<uint32_t>();
+    r.codes = ix.codes.as<uint8_t>();
+    r.cross = ix.cross.as<float>();
+    r.ids = ix.ids.as<int32_t>();
+    r.out_ids = out_ids + c0 * k;
+    r.out_dists = out_dists + c0 * k;
+    launch_rescore(r, st);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // File format: magic, version, params, n_points, then sections
 // (u64 size, bytes, u64 FNV-1a checksum).
 // ---------------------------------------------------------------------------
@@ -537,6 +642,24 @@ int bpq_search(const bpq_index* ix, const float* q, int64_t nq, const int64_t* L
     DeviceGuard dg(ix->device);
     run_queries(*ix, q, nq, L_host, L_stride, k, scorer, ids, dists, nullptr, 0, nullptr, nullptr, ws, ws_bytes,
                 static_cast<cudaStream_t>(stream));
+  });
+}
+
+size_t bpq_search_shortlist_workspace_size(const bpq_index* ix, int64_t nq, int64_t L_max, int32_t shortlist) {
+  if (!ix || nq < 0 || L_max < 1 || shortlist < 1 || shortlist > MAX_K) return 0;
+  return shortlist_layout(*ix, std::max<int64_t>(nq, 1), L_max, shortlist).total;
+}
+
+int bpq_search_shortlist(const bpq_index* ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride,
+                         int32_t k, int32_t shortlist, int32_t lut_precision, int32_t* ids, float* dists, void* ws,
+                         size_t ws_bytes, void* stream) {
+  return guard([&] {
+    check_searchable(ix);
+    BPQ_CHECK(nq >= 0, BPQ_EINVAL, "nq < 0");
+    BPQ_CHECK(lut_precision == BPQ_LUT_I8, BPQ_EINVAL, "lut_precision must be BPQ_LUT_I8");
+    DeviceGuard dg(ix->device);
+    run_shortlist(*ix, q, nq, L_host, L_stride, k, shortlist, ids, dists, ws, ws_bytes,
+                  static_cast<cudaStream_t>(stream));
   });
 }
 

@@ -261,6 +261,18 @@ __device__ void block_topk_prune(BlockTopK<NT>& tk, int k) {
   __syncthreads();
 }
 
+// Final, raw: the first k composites of the exact order (EMPTY padded).
+template <int NT>
+__device__ void block_topk_finish_raw(BlockTopK<NT>& tk, int k, uint64_t* out) {
+  block_topk_prune<NT>(tk, k);
+  const int n = *tk.nbuf;
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  for (int e = n + threadIdx.x; e < n2; e += NT) tk.buf[e] = EMPTY;
+  block_bitonic_sort(tk.buf, n2);
+  for (int r = threadIdx.x; r < k; r += NT) out[r] = r < n ? tk.buf[r] : EMPTY;
+}
+
 // Final: exact (distance, id) order of the buffer, first k written out.
 template <int NT>
 __device__ void block_topk_finish(BlockTopK<NT>& tk, int k, int32_t* out_ids, float* out_dists) {
@@ -279,11 +291,16 @@ __device__ void block_topk_finish(BlockTopK<NT>& tk, int k, int32_t* out_ids, fl
 
 // ---------------------------------------------------------------------------
 // FBPQ scan: one CTA per query.
-//  POINT = true : per-point cross term (one coalesced float per candidate)
-//  POINT = false: cross terms gathered from the X1 / X2 tables (2M lookups)
+//  FB_POINT : per-point cross term (one coalesced float per candidate)
+//  FB_TABLES: cross terms gathered from the X1 / X2 tables (2M lookups)
+//  FB_Q8    : int8 table (bpq_search_shortlist): score (key + cross) + s * sum of
+//             M int8 entries, ranked by (score, list position); no id is read
 // ---------------------------------------------------------------------------
-template <int M, bool POINT>
+enum { FB_POINT = 0, FB_TABLES = 1, FB_Q8 = 2 };
+
+template <int M, int VAR>
 __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
+  constexpr bool POINT = VAR != FB_TABLES, Q8 = VAR == FB_Q8;
   constexpr int NT = 256, NW = NT / 32, CH = NT, ILP = 4, M2 = M / 2;
   constexpr int SUB = 4096;          // candidates per cell-map refresh
   constexpr int PER = SUB / NT;      // candidates per thread in the map
@@ -304,9 +321,15 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
   const int lane = threadIdx.x & 31;
   const int k = a.k;
 
+  const uint8_t* lut8 = reinterpret_cast<const uint8_t*>(lut);
   for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
     __syncthreads();
-    {
+    float scale = 0.f;
+    if (Q8) {
+      const uint4* src = reinterpret_cast<const uint4*>(a.lut8 + q * M * KSUB);
+      for (int t = threadIdx.x; t < M * KSUB / 16; t += NT) reinterpret_cast<uint4*>(lut)[t] = src[t];
+      scale = a.lut_scale[q];
+    } else {
       const float4* src = reinterpret_cast<const float4*>(a.lut + q * M * KSUB);
       for (int t = threadIdx.x; t < M * KSUB / 4; t += NT) reinterpret_cast<float4*>(lut)[t] = src[t];
     }
@@ -379,7 +402,12 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
             if (cidx[u] >= 0) {
               const int c = cidx[u];
               float part;
-              if (POINT) {
+              if (Q8) {
+                int isum = 0;
+#pragma unroll
+                for (int kk = 0; kk < M; ++kk) isum += lut8[kk * KSUB + code[u].byte(kk)];
+                part = __fmul_rn(scale, (float)isum);
+              } else if (POINT) {
                 part = pc[u];
 #pragma unroll
                 for (int kk = 0; kk < M; ++kk) part += lut[kk * KSUB + code[u].byte(kk)];
@@ -394,10 +422,10 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
                   part += lut[kk * KSUB + b] + xv;
                 }
               }
-              const float dist = c_key[c] + part;
+              const float dist = Q8 ? __fadd_rn(__fadd_rn(c_key[c], pc[u]), part) : c_key[c] + part;
               const uint32_t o = f2ord(dist);
               if (o <= th_hi) {
-                comp = ((uint64_t)o << 32) | (uint32_t)__ldg(a.ids + pos[u]);
+                comp = ((uint64_t)o << 32) | (Q8 ? pos[u] : (uint32_t)__ldg(a.ids + pos[u]));
                 acc = comp <= th;
               }
             }
@@ -415,7 +443,58 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
         __syncthreads();
       }
     }
-    block_topk_finish<NT>(tk, k, a.out_ids + q * k, a.out_dists + q * k);
+    if (Q8)
+      block_topk_finish_raw<NT>(tk, k, a.sl_out + q * k);
+    else
+      block_topk_finish<NT>(tk, k, a.out_ids + q * k, a.out_dists + q * k);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Exact re-score of a shortlist (bpq_search_shortlist step 3): one CTA per
+// query; each shortlisted list position finds its cell by binary search on the
+// offsets, then its FBPQ distance (Eqs. 8-9) is formed exactly as in the FP32
+// scan: key(i, j) + (cross(p) + lut[0][c_0] + ... + lut[M-1][c_{M-1}]).
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(256) rescore_kernel(RescoreArgs r) {
+  constexpr int NT = 256;
+  using TK = BlockTopK<NT>;
+  __shared__ uint64_t bufs[2 * TK::CAP];
+  __shared__ unsigned long long thr;
+  __shared__ int nbuf;
+  __shared__ uint32_t hist[260];
+  const uint32_t ncell = (uint32_t)r.T * (uint32_t)r.T;
+  for (int64_t q = blockIdx.x; q < r.nq; q += gridDim.x) {
+    __syncthreads();
+    TK tk{bufs, bufs + TK::CAP, &nbuf, &thr, hist};
+    if (threadIdx.x == 0) {
+      thr = EMPTY;
+      nbuf = 0;
+    }
+    __syncthreads();
+    const float* lut = r.lut + q * M * KSUB;
+    for (int e = threadIdx.x; e < r.S; e += NT) {
+      const uint64_t s = r.sl[q * r.S + e];
+      if (s == EMPTY) continue;
+      const uint32_t pos = (uint32_t)s;
+      uint32_t lo = 0, hi = ncell;  // last cell with offsets[cell] <= pos
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(r.offsets + mid) <= pos) lo = mid; else hi = mid;
+      }
+      const uint32_t i = lo / (uint32_t)r.T, j = lo % (uint32_t)r.T;
+      const float key = __fadd_rn(r.d1[q * r.T + i], r.d2[q * r.T + j]);
+      Code<M> code;
+      code.load(r.codes, pos);
+      float part = __ldg(r.cross + pos);
+#pragma unroll
+      for (int kk = 0; kk < M; ++kk) part += __ldg(lut + kk * KSUB + code.byte(kk));
+      const float dist = key + part;
+      tk.buf[atomicAdd(&nbuf, 1)] = ((uint64_t)f2ord(dist) << 32) | (uint32_t)__ldg(r.ids + pos);
+    }
+    __syncthreads();
+    block_topk_finish<NT>(tk, r.k, r.out_ids + q * r.k, r.out_dists + q * r.k);
   }
 }
 
@@ -545,10 +624,10 @@ __global__ void __launch_bounds__(NW * 32) recon_scan_kernel(ScanArgs a) {
   }
 }
 
-template <int M, bool POINT>
+template <int M, int VAR>
 void run_fbpq(const ScanArgs& a, cudaStream_t st) {
   const size_t smem = (size_t)M * KSUB * 4 + (size_t)2 * BlockTopK<256>::CAP * 8 + 4096;
-  auto kern = fbpq_scan_kernel<M, POINT>;
+  auto kern = fbpq_scan_kernel<M, VAR>;
   BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
   kern<<<grid, 256, smem, st>>>(a);
@@ -573,9 +652,9 @@ void run_recon(const ScanArgs& a, cudaStream_t st) {
 template <int M, int SUB, int KP>
 void dispatch_scorer(const ScanArgs& a, int scorer, cudaStream_t st) {
   if (scorer == BPQ_SCORER_FBPQ)
-    run_fbpq<M, true>(a, st);
+    run_fbpq<M, FB_POINT>(a, st);
   else if (scorer == BPQ_SCORER_FBPQ_TABLES)
-    run_fbpq<M, false>(a, st);
+    run_fbpq<M, FB_TABLES>(a, st);
   else if (scorer == BPQ_SCORER_RECON)
     run_recon<M, SUB, KP, false>(a, st);
   else
@@ -593,6 +672,24 @@ void dispatch_k(const ScanArgs& a, int scorer, cudaStream_t st) {
 
 bool scan_supported(int D, int M) {
   return (D == 128 && (M == 8 || M == 16)) || (D == 32 && M == 8) || (D == 8 && M == 8);
+}
+
+void launch_scan_q8(const ScanArgs& a, cudaStream_t st) {
+  if (a.nq <= 0) return;
+  BPQ_CHECK(a.k >= 1 && a.k <= MAX_K, BPQ_EINVAL, "shortlist must be in [1, 1024]");
+  BPQ_CHECK(a.D == 128 && (a.M == 8 || a.M == 16), BPQ_EINVAL, "the int8 scan is built for D = 128, M = 8 or 16");
+  if (a.M == 8) run_fbpq<8, FB_Q8>(a, st);
+  else run_fbpq<16, FB_Q8>(a, st);
+}
+
+void launch_rescore(const RescoreArgs& r, cudaStream_t st) {
+  if (r.nq <= 0) return;
+  BPQ_CHECK(r.S >= 1 && r.S <= MAX_K && r.k >= 1 && r.k <= r.S, BPQ_EINVAL, "need 1 <= k <= shortlist <= 1024");
+  const int grid = (int)std::min<int64_t>(r.nq, 1 << 20);
+  if (r.M == 8) rescore_kernel<8><<<grid, 256, 0, st>>>(r);
+  else if (r.M == 16) rescore_kernel<16><<<grid, 256, 0, st>>>(r);
+  else throw Error(BPQ_EINVAL, "the re-score kernel is built for M = 8 or 16");
+  check_launch("re-score kernel");
 }
 
 void launch_scan(const ScanArgs& a, int scorer, cudaStream_t st) {

@@ -12,6 +12,8 @@
 //                                                       + sum_{k>=M/2} X2[j][k-M/2][r_k].
 // For integer-valued inputs (queries in [0, 255], integer codebooks) every
 // product and partial sum here is an integer below 2^24, so FP32 is exact.
+#include <algorithm>
+
 #include "bpq_internal.cuh"
 
 namespace bpq {
@@ -108,7 +110,59 @@ __global__ void cross_table_kernel(const float* __restrict__ C, const float* __r
   X[e] = 2.f * acc;
 }
 
+// bpq_search_shortlist step 1: per query, lo_k = min_t lut[k][t], step
+// s = max_k (max_t lut[k][t] - lo_k) / 255 (1 if that is 0), and
+// q8[k][t] = round_half_even((lut[k][t] - lo_k) / s), all in IEEE FP32.
+template <int M>
+__global__ void __launch_bounds__(256) quant_lut_kernel(const float* __restrict__ lut, int64_t nq,
+                                                        uint8_t* __restrict__ lut8, float* __restrict__ scale) {
+  __shared__ float lo_s[M];
+  __shared__ unsigned int range_bits;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t q = blockIdx.x; q < nq; q += gridDim.x) {
+    const float* L = lut + q * M * KSUB;
+    __syncthreads();
+    if (threadIdx.x == 0) range_bits = 0u;
+    __syncthreads();
+    for (int k = warp; k < M; k += 8) {
+      float mn = __int_as_float(0x7f800000), mx = -__int_as_float(0x7f800000);
+      for (int t = lane; t < KSUB; t += 32) {
+        const float v = L[k * KSUB + t];
+        mn = fminf(mn, v);
+        mx = fmaxf(mx, v);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      }
+      if (lane == 0) {
+        lo_s[k] = mn;
+        atomicMax(&range_bits, __float_as_uint(__fsub_rn(mx, mn)));  // >= 0: bit order = value order
+      }
+    }
+    __syncthreads();
+    const float range = __uint_as_float(range_bits);
+    const float s = range > 0.f ? __fdiv_rn(range, 255.f) : 1.f;
+    for (int e = threadIdx.x; e < M * KSUB; e += 256) {
+      const float x = __fsub_rn(L[e], lo_s[e / KSUB]);
+      const int v = __float2int_rn(__fdiv_rn(x, s));
+      lut8[q * M * KSUB + e] = (uint8_t)min(255, max(0, v));
+    }
+    if (threadIdx.x == 0) scale[q] = s;
+  }
+}
+
 }  // namespace
+
+void launch_quant_lut(const float* lut, int M, int64_t nq, uint8_t* lut8, float* scale, cudaStream_t st) {
+  if (nq <= 0) return;
+  const int grid = (int)std::min<int64_t>(nq, 1 << 20);
+  if (M == 8) quant_lut_kernel<8><<<grid, 256, 0, st>>>(lut, nq, lut8, scale);
+  else if (M == 16) quant_lut_kernel<16><<<grid, 256, 0, st>>>(lut, nq, lut8, scale);
+  else throw Error(BPQ_EINVAL, "the int8 table is built for M = 8 or 16");
+  check_launch("table quantization kernel");
+}
 
 void launch_query_tables(const bpq_index& ix, const float* q, int64_t nq, float* d1, float* d2,
                          float* lut, cudaStream_t st) {

@@ -186,4 +186,12 @@ TINY = Workload("tiny-100k-T64-M8", n_base=100_000, n_learn=20_000, n_query=100,
                 n_comp=64, T=64, M=8, L=(10_000,), k=100)
 SIFT10M = Workload("sift10m-T1024-M8", n_base=10_000_000, n_learn=1_024_000, n_query=10_000,
                    n_comp=1024, T=1024, M=8, L=(1_000, 10_000, 100_000), k=100)
-WORKLOADS = {w.name: w for w in (TINY, SIFT10M)}
+# 100M points with M = 16 (the precision-variant shape), 100M points with M = 8
+# (uneven budgets, local codebooks) and 1B points (the serving shape).
+SIFT100M_M16 = Workload("sift100m-T1024-M16", n_base=100_000_000, n_learn=1_024_000, n_query=10_000,
+                        n_comp=1024, T=1024, M=16, L=(30_000,), k=100)
+SIFT100M = Workload("sift100m-T1024-M8", n_base=100_000_000, n_learn=1_024_000, n_query=10_000,
+                    n_comp=1024, T=1024, M=8, L=(1_000, 100_000), k=100)
+SIFT1B = Workload("sift1b-T1024-M8", n_base=1_000_000_000, n_learn=1_024_000, n_query=10_000,
+                  n_comp=4096, T=1024, M=8, L=(1_000, 10_000, 100_000), k=100)
+WORKLOADS = {w.name: w for w in (TINY, SIFT10M, SIFT100M_M16, SIFT100M, SIFT1B)}

@@ -1,0 +1,84 @@
+"""GPU parity of the int8-table shortlist search (bpq_search_shortlist) and of the
+M = 16 scans against the FP64 oracle, on the tiny workload (100k points, T = 64)."""
+import numpy as np
+import pytest
+
+from oracle import bpq_oracle as O
+from tests.parity import assert_topk_match
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def _gpu_index(cb, base):
+    import paper_1404_1831_gb300 as bpq
+    ix = bpq.Index.create(cb.C1, cb.C2, cb.R)
+    ix.add(torch.as_tensor(base, dtype=torch.float32, device=DEV))
+    ix.finalize()
+    return ix
+
+
+@pytest.fixture(scope="module")
+def m8(tiny_oracle):
+    t = tiny_oracle
+    return dict(ix=_gpu_index(t["cb"], t["base"]), index=t["index"], qh=t["queries"],
+                q=torch.as_tensor(t["queries"], dtype=torch.float32, device=DEV))
+
+
+@pytest.fixture(scope="module")
+def m16(tiny_oracle):
+    t = tiny_oracle
+    w = t["w"]
+    cb = O.train_multi_d_adc(t["learn"], w.T, 16, w.kmeans_iters)
+    index = O.build_index(cb, t["base"])
+    return dict(ix=_gpu_index(cb, t["base"]), index=index, qh=t["queries"][:40],
+                q=torch.as_tensor(t["queries"][:40], dtype=torch.float32, device=DEV))
+
+
+def _check(fx, L, k, S, nq=None):
+    nq = nq or len(fx["qh"])
+    ids, dists = fx["ix"].search_shortlist(fx["q"][:nq], L, k, shortlist=S)
+    o_ids, o_d = O.search_shortlist(fx["index"], fx["qh"][:nq], L, k, S)
+    ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+    assert np.array_equal(ids, o_ids), "shortlist ids differ"
+    assert np.array_equal(dists.astype(np.float64), o_d), "shortlist distances differ"
+    return ids, dists
+
+
+@pytest.mark.parametrize("L,k,S", [(10_000, 100, 1000), (3_000, 10, 100), (10_000, 100, 100), (20_000, 1, 1024)])
+def test_shortlist_matches_oracle_m8(m8, L, k, S):
+    _check(m8, L, k, S, nq=40)
+
+
+def test_shortlist_pads_when_few_candidates(m8):
+    ids, dists = _check(m8, 1, 100, 1000, nq=10)
+    assert (ids == -1).any() and np.isinf(dists).any()
+
+
+def test_full_shortlist_equals_fbpq_search(m8):
+    """A shortlist as long as the candidate list (L' < 1024 at L = 500) returns the
+    FP32 FBPQ search's lists."""
+    a = [t.cpu().numpy() for t in m8["ix"].search(m8["q"], 500, 50, "fbpq")]
+    b = [t.cpu().numpy() for t in m8["ix"].search_shortlist(m8["q"], 500, 50, shortlist=1024)]
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_fbpq_and_reconstruction_match_oracle_m16(m16):
+    for scorer, o_scorer in (("fbpq", "fbpq"), ("fbpq_tables", "fbpq"), ("recon", "recon")):
+        ids, dists = m16["ix"].search(m16["q"], 5_000, 50, scorer)
+        o_ids, o_d, _ = O.search(m16["index"], m16["qh"], 5_000, 50, o_scorer)
+        exact = assert_topk_match(ids.cpu().numpy(), dists.cpu().numpy(), o_ids, o_d)
+        assert exact == len(o_ids)
+
+
+def test_shortlist_matches_oracle_m16(m16):
+    _check(m16, 10_000, 100, 1000)
+
+
+def test_shortlist_rejects_bad_arguments(m8):
+    import paper_1404_1831_gb300 as bpq
+    for k, S in ((100, 50), (10, 1025), (0, 10)):
+        with pytest.raises(bpq.BpqError):
+            m8["ix"].search_shortlist(m8["q"][:2], 1000, k, shortlist=S)
