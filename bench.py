@@ -248,6 +248,7 @@ def run_ours(args):
     torch.backends.cuda.matmul.allow_tf32 = False
 
     import paper_1404_1831_gb300 as bpq
+    from paper_1404_1831_gb300 import multi
     import synthdata as sd
     from synthdata import device as sdev
 
@@ -266,7 +267,8 @@ def run_ours(args):
     ix.finalize()
     info = ix.info()
     nq = w.n_query
-    queries = sdev.points_cuda(mix, sd.STREAM_QUERY, rank * nq, nq, device=dev)
+    q0, _ = multi.replica_queries(rank, nq)  # replicas: every rank answers its own batch
+    queries = sdev.points_cuda(mix, sd.STREAM_QUERY, q0, nq, device=dev)
     torch.cuda.synchronize()
     setup_s = time.time() - t_setup
 
@@ -344,9 +346,7 @@ def run_ours(args):
     ix.search_status(ws)
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = multi.max_over_ranks(total_ms, device=dev)
     value = nq * world * args.steps / (total_ms / 1e3)
     ms_per_step = total_ms / args.steps
 
@@ -372,9 +372,7 @@ def run_ours(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_total = sum(e2e_ms)
     if world > 1:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+        e2e_total = multi.max_over_ranks(e2e_total, device=dev)
     e2e = {"value": nq * world * args.steps / (e2e_total / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": nq * w.dim * 4, "d2h_bytes_per_step": nq * k * 8,
            "ms_per_step": e2e_total / args.steps}

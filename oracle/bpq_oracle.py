@@ -519,14 +519,17 @@ def build_index(cb: Codebooks, X, ids=None, variant="global"):
     return OracleIndex(cb=cb, lists=build_lists(cells, codes, ids, cb.T), variant=variant, tables=tab)
 
 
-def search_one(index: OracleIndex, q, L, k, scorer="fbpq", traversal="multisequence"):
+def search_one(index: OracleIndex, q, L, k, scorer="fbpq", traversal="multisequence", cut_counts=None):
     """One query of §2.3.3 / §3.1 / §3.2: coarse distances, traversal until L points,
     distances of all candidates with the chosen scorer, rerank by (distance, id).
+    cut_counts: per-cell counts the stopping rule uses instead of the index's own
+    (a shard of a larger index traverses with the whole index's counts).
     Returns (ids (k,), dists (k,), visited cell ids, L')."""
     cb, lists = index.cb, index.lists
     d1, d2 = coarse_distances(q, cb)
     walk = traverse_multisequence if traversal == "multisequence" else traverse_full_sort
-    cells, _, total = walk(d1, d2, lists.counts(), L)
+    counts = lists.counts() if cut_counts is None else np.asarray(cut_counts)
+    cells, _, total = walk(d1, d2, counts, L)
     pos = candidates(cells, lists)
     cell_of = np.repeat(cells, lists.counts()[cells])
     codes = lists.codes[pos]
