@@ -728,7 +728,8 @@ int bpq_get_info(const bpq_index* ix, bpq_info* out) {
     out->device_bytes = (int64_t)(ix->C1.bytes + ix->C2.bytes + ix->R.bytes + ix->Q.bytes + ix->S.bytes +
                                   ix->X1.bytes + ix->X2.bytes + ix->offsets.bytes + ix->codes.bytes +
                                   ix->ids.bytes + ix->cross.bytes + ix->pend_cells.bytes + ix->pend_codes.bytes +
-                                  ix->pend_ids.bytes);
+                                  ix->pend_ids.bytes + ix->C1b.bytes + ix->C2b.bytes + ix->Rb.bytes + ix->n1.bytes +
+                                  ix->n2.bytes + ix->nR.bytes);
     out->params = ix->p;
   });
 }

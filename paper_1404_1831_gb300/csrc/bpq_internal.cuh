@@ -177,6 +177,12 @@ struct bpq_index {
   // finalized lists
   bpq::DevBuf offsets, codes, ids;
   bpq::DevBuf cross;  // per point 2<c_ij, r> (global variant)
+  // tensor-core operands of the query tables: BF16 copies of C1, C2 (T x kh) and
+  // R (M x 256 x ks), K padded with zeros to kh = 16 ceil(D/32), ks = 16 ceil(D/M/16),
+  // FP32 squared norms of their rows, and whether every copy is exact
+  bpq::DevBuf C1b, C2b, Rb, n1, n2, nR;
+  int kh = 0, ks = 0;
+  bool coarse_bf16_exact = false, R_bf16_exact = false;
   int64_t n_points = 0, n_nonempty = 0, max_cell = 0;
   // workspace owned by bpq_search_host
   bpq::DevBuf host_ws, host_q, host_ids, host_dists;

@@ -12,6 +12,8 @@
 //                                                       + sum_{k>=M/2} X2[j][k-M/2][r_k].
 // For integer-valued inputs (queries in [0, 255], integer codebooks) every
 // product and partial sum here is an integer below 2^24, so FP32 is exact.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "bpq_internal.cuh"
@@ -19,79 +21,214 @@
 namespace bpq {
 namespace {
 
-constexpr int BM = 64;   // table rows (queries) per CTA
-constexpr int BN = 64;   // table columns (codewords) per CTA
-constexpr int BK = 16;   // dimensions per shared-memory step
 constexpr int MAXP = 18; // problems per launch (2 halves, or up to 16 sub-quantizers)
 
 enum { MODE_SQ = 0, MODE_LUT = 1 };
 
-struct PairProblem {
-  const float* B;  // nb x dim codewords, dense
-  float* out;      // out[a * ldo + o_off + b]
-  int a_off;       // first query column of this problem
-  int nb;
-  int dim;
-  int ldo;
-  int o_off;
+// ---------------------------------------------------------------------------
+// Tensor-core tables (tcgen05, BF16 operands, FP32 accumulation in tensor
+// memory).  One CTA of 128 threads computes a tile of 128 queries x up to 256
+// codewords of one problem: D = A B^T with A the query slice and B the codewords
+// (BF16 copies made at index build), then out = ||a||^2 + ||b||^2 - 2 D (coarse
+// tables) or ||b||^2 - 2 D (PQ table).  Integer inputs of magnitude <= 256 are
+// exact in BF16, every product is below 2^16 and every partial sum below 2^24,
+// so the FP32 accumulation and the epilogue are exact.  A tile whose operands
+// are not all exact in BF16 is computed in FP32 on the CUDA cores instead, so the
+// tables never lose precision.
+// Operands are K-major in shared memory without swizzle: 8-row x 16-byte core
+// matrices, core (row group g, column group c) at byte 128 (g * KB + c).
+// ---------------------------------------------------------------------------
+constexpr int TC_M = 128, TC_N = 256;
+
+struct TcProblem {
+  const __nv_bfloat16* Bb;  // nb x kpad BF16, zero padded
+  const float* B;           // nb x dim FP32
+  const float* bn;          // nb squared norms
+  float* out;               // out[a * ldo + o_off + b]
+  int a_off, nb, dim, kpad, ldo, o_off, b_exact;
 };
-struct PairProblems {
-  PairProblem p[MAXP];
+struct TcProblems {
+  TcProblem p[MAXP];
 };
 
-// out[a][b] = sum_d f(A[a][a_off + d], B[b][d]) with f = (a-b)^2 or b(b - 2a).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t core_off(int r, int k, int KB) {
+  return (uint32_t)((((r >> 3) * KB + (k >> 3)) * 128) + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (row-group)
+// byte offsets, the fixed 0b001 at bits 46-48, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(256) pair_table_kernel(const float* __restrict__ A, int lda, int na,
-                                                         PairProblems probs) {
-  const PairProblem pr = probs.p[blockIdx.z];
-  const int b0 = blockIdx.x * BN;
-  if (b0 >= pr.nb) return;
-  const int a0 = blockIdx.y * BM;
-  __shared__ float As[BK][BM + 1];
-  __shared__ float Bs[BK][BN + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float acc[4][4] = {};
-  for (int d0 = 0; d0 < pr.dim; d0 += BK) {
-    for (int e = threadIdx.x; e < BM * BK; e += 256) {
-      int r = e / BK, d = e % BK;
-      int a = a0 + r;
-      As[d][r] = (a < na && d0 + d < pr.dim) ? A[(int64_t)a * lda + pr.a_off + d0 + d] : 0.f;
-      int b = b0 + r;
-      Bs[d][r] = (b < pr.nb && d0 + d < pr.dim) ? pr.B[(int64_t)b * pr.dim + d0 + d] : 0.f;
+__global__ void __launch_bounds__(128) tc_table_kernel(const float* __restrict__ A, int lda, int na,
+                                                       TcProblems probs) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ float bn_s[TC_N];
+  const TcProblem pr = probs.p[blockIdx.z];
+  const int n0 = blockIdx.x * TC_N;
+  if (n0 >= pr.nb) return;
+  const int a0 = blockIdx.y * TC_M;
+  const int nt = min(TC_N, (pr.nb - n0 + 31) & ~31);  // tile columns: MMA N, a multiple of 32
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int kpad = pr.kpad, KB = kpad >> 3;
+  unsigned char* sA = tsm;
+  unsigned char* sB = tsm + TC_M * kpad * 2;
+  int bad = 0;
+  if (((pr.dim | lda | pr.a_off) & 3) == 0) {  // query slices as float4 groups (kpad is a power of two)
+    const int sh = __ffs(kpad >> 2) - 1;
+    for (int e = tid; e < (TC_M * kpad) >> 2; e += 128) {
+      const int r = e >> sh, k = (e & ((kpad >> 2) - 1)) << 2;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (a0 + r < na && k < pr.dim) v = *reinterpret_cast<const float4*>(A + (int64_t)(a0 + r) * lda + pr.a_off + k);
+      const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+      bad |= __low2float(lo) != v.x || __high2float(lo) != v.y || __low2float(hi) != v.z || __high2float(hi) != v.w;
+      uint2 pk;
+      pk.x = *reinterpret_cast<const uint32_t*>(&lo);
+      pk.y = *reinterpret_cast<const uint32_t*>(&hi);
+      *reinterpret_cast<uint2*>(sA + core_off(r, k, KB)) = pk;
     }
+  } else {
+    for (int e = tid; e < TC_M * kpad; e += 128) {
+      const int r = e / kpad, k = e - r * kpad;
+      const float v = (a0 + r < na && k < pr.dim) ? A[(int64_t)(a0 + r) * lda + pr.a_off + k] : 0.f;
+      const __nv_bfloat16 b = __float2bfloat16_rn(v);
+      bad |= __bfloat162float(b) != v;
+      *reinterpret_cast<__nv_bfloat16*>(sA + core_off(r, k, KB)) = b;
+    }
+  }
+  {  // codewords: one 16-byte core row per step
+    const int sh = __ffs(kpad >> 3) - 1;
+    for (int e = tid; e < (nt * kpad) >> 3; e += 128) {
+      const int r = e >> sh, k = (e & ((kpad >> 3) - 1)) << 3;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (n0 + r < pr.nb) v = *reinterpret_cast<const uint4*>(pr.Bb + (int64_t)(n0 + r) * kpad + k);
+      *reinterpret_cast<uint4*>(sB + core_off(r, k, KB)) = v;
+    }
+  }
+  for (int c = tid; c < nt; c += 128) bn_s[c] = n0 + c < pr.nb ? pr.bn[n0 + c] : 0.f;
+  bad = __syncthreads_or(bad) || !pr.b_exact;
+  const int row = warp * 32 + lane, ga = a0 + row;
+  bool done = false;
+  if (!bad) {
+    const uint32_t ncols = nt <= 32 ? 32u : (nt <= 64 ? 64u : (nt <= 128 ? 128u : 256u));
+    if (warp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                   "r"(ncols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+      asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    const int dn = min(BK, pr.dim - d0);
-    for (int d = 0; d < dn; ++d) {
-      float av[4], bv[4];
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tm = tmem_base;
+    // D FP32 (bits 4-5), A and B BF16 (bits 7-9, 10-12), both K-major, N >> 3 (bits 17-22), M >> 4 (bits 24-28)
+    const uint32_t idesc =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+    if (tid == 0) {
+      for (int kk = 0; kk < kpad / 16; ++kk) {
+        const uint64_t ad = smem_desc(smem_u32(sA) + kk * 256, 128, KB * 128);
+        const uint64_t bd = smem_desc(smem_u32(sB) + kk * 256, 128, KB * 128);
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                     ::"r"(tm), "l"(ad), "l"(bd), "r"(idesc), "r"(kk > 0 ? 1u : 0u));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar)));
+    }
+    uint32_t ready = 0;
+    for (int it = 0; it < (1 << 24) && !ready; ++it)  // bounded: an MMA group takes microseconds
+      asm volatile("{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\nselp.u32 %0, 1, 0, P;\n}\n"
+                   : "=r"(ready) : "r"(smem_u32(&mbar)), "r"(0));
+    done = __syncthreads_and(ready);
+    if (done) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      float an = 0.f;
+      if (MODE == MODE_SQ) {
+        for (int k = 0; k < pr.dim; ++k) {
+          const float v = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(sA + core_off(row, k, KB)));
+          an = fmaf(v, v, an);
+        }
+      }
+      const bool vec = ((pr.ldo | pr.o_off) & 3) == 0;
+      for (int c0 = 0; c0 < nt; c0 += 32) {
+        uint32_t r[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(tm + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (ga < na) {
+          float* o = pr.out + (int64_t)ga * pr.ldo + pr.o_off + n0 + c0;
+          float v[32];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) av[r] = As[d][ty + 16 * r];
+          for (int j = 0; j < 32; ++j) {
+            const float bn = bn_s[c0 + j];
+            const float d2 = 2.f * __uint_as_float(r[j]);
+            v[j] = (MODE == MODE_SQ) ? __fsub_rn(__fadd_rn(an, bn), d2) : __fsub_rn(bn, d2);
+          }
+          if (vec && n0 + c0 + 32 <= pr.nb) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) bv[c] = Bs[d][tx + 16 * c];
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          if (MODE == MODE_SQ) {
-            float t = av[r] - bv[c];
-            acc[r][c] = fmaf(t, t, acc[r][c]);
+            for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
           } else {
-            float t = fmaf(-2.f, av[r], bv[c]);
-            acc[r][c] = fmaf(bv[c], t, acc[r][c]);
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (n0 + c0 + j < pr.nb) o[j] = v[j];
           }
         }
+      }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(ncols));
   }
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    int a = a0 + ty + 16 * r;
-    if (a >= na) continue;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      int b = b0 + tx + 16 * c;
-      if (b < pr.nb) pr.out[(int64_t)a * pr.ldo + pr.o_off + b] = acc[r][c];
+  if (!done && ga < na) {  // FP32 on the CUDA cores: sum (a - b)^2, or sum b (b - 2a)
+    const float* a = A + (int64_t)ga * lda + pr.a_off;
+    for (int b = n0; b < min(pr.nb, n0 + nt); ++b) {
+      const float* bb = pr.B + (int64_t)b * pr.dim;
+      float acc = 0.f;
+      for (int d = 0; d < pr.dim; ++d) {
+        if (MODE == MODE_SQ) {
+          const float t = a[d] - bb[d];
+          acc = fmaf(t, t, acc);
+        } else {
+          acc = fmaf(bb[d], fmaf(-2.f, a[d], bb[d]), acc);
+        }
+      }
+      pr.out[(int64_t)ga * pr.ldo + pr.o_off + b] = acc;
     }
   }
+}
+
+// BF16 copy (K padded to kpad) and squared norms of n rows of dim floats; sets
+// *inexact if a value is not exactly representable in BF16.
+__global__ void bf16_rows_kernel(const float* __restrict__ X, int64_t n, int dim, int kpad,
+                                 __nv_bfloat16* __restrict__ Xb, float* __restrict__ norms, int* inexact) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  float s = 0.f;
+  int bad = 0;
+  for (int k = 0; k < kpad; ++k) {
+    const float v = k < dim ? X[r * dim + k] : 0.f;
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    bad |= __bfloat162float(b) != v;
+    Xb[r * kpad + k] = b;
+    s = fmaf(v, v, s);
+  }
+  norms[r] = s;
+  if (bad) atomicExch(inexact, 1);
 }
 
 // X[i][k][t] = 2 * sum_d C[i][k*s + d] * R[kbase + k][t][d]
@@ -168,25 +305,35 @@ void launch_query_tables(const bpq_index& ix, const float* q, int64_t nq, float*
                          float* lut, cudaStream_t st) {
   if (nq <= 0) return;
   const int D = ix.p.D, T = ix.p.T, M = ix.p.M;
-  const int gy = (int)((nq + BM - 1) / BM);
-  BPQ_CHECK(nq < (int64_t)65535 * BM, BPQ_EINVAL, "too many queries in one table launch");
+  const int ty = (int)((nq + TC_M - 1) / TC_M);
+  BPQ_CHECK(nq < (int64_t)65535 * TC_M, BPQ_EINVAL, "too many queries in one table launch");
   if (d1 || d2) {
-    PairProblems pp{};
+    TcProblems pp{};
     int np = 0;
-    if (d1) pp.p[np++] = PairProblem{ix.C1.as<float>(), d1, 0, T, ix.h, T, 0};
-    if (d2) pp.p[np++] = PairProblem{ix.C2.as<float>(), d2, ix.h, T, ix.h, T, 0};
-    dim3 grid((T + BN - 1) / BN, gy, np);
-    pair_table_kernel<MODE_SQ><<<grid, 256, 0, st>>>(q, D, (int)nq, pp);
+    const int ex = ix.coarse_bf16_exact ? 1 : 0;
+    if (d1)
+      pp.p[np++] = TcProblem{ix.C1b.as<__nv_bfloat16>(), ix.C1.as<float>(), ix.n1.as<float>(), d1, 0, T, ix.h, ix.kh,
+                             T, 0, ex};
+    if (d2)
+      pp.p[np++] = TcProblem{ix.C2b.as<__nv_bfloat16>(), ix.C2.as<float>(), ix.n2.as<float>(), d2, ix.h, T, ix.h,
+                             ix.kh, T, 0, ex};
+    const size_t smem = (size_t)(TC_M + TC_N) * ix.kh * 2;
+    BPQ_CUDA(cudaFuncSetAttribute(tc_table_kernel<MODE_SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((T + TC_N - 1) / TC_N, ty, np);
+    tc_table_kernel<MODE_SQ><<<grid, 128, smem, st>>>(q, D, (int)nq, pp);
     check_launch("coarse table kernel");
   }
   if (lut) {
     BPQ_CHECK(M <= MAXP, BPQ_EINVAL, "M too large for the table kernel");
-    PairProblems pp{};
+    TcProblems pp{};
+    const int ex = ix.R_bf16_exact ? 1 : 0;
     for (int k = 0; k < M; ++k)
-      pp.p[k] = PairProblem{ix.R.as<float>() + (int64_t)k * KSUB * ix.s, lut, k * ix.s, KSUB, ix.s,
-                            M * KSUB, k * KSUB};
-    dim3 grid(KSUB / BN, gy, M);
-    pair_table_kernel<MODE_LUT><<<grid, 256, 0, st>>>(q, D, (int)nq, pp);
+      pp.p[k] = TcProblem{ix.Rb.as<__nv_bfloat16>() + (int64_t)k * KSUB * ix.ks, ix.R.as<float>() + (int64_t)k * KSUB * ix.s,
+                          ix.nR.as<float>() + (int64_t)k * KSUB, lut, k * ix.s, KSUB, ix.s, ix.ks, M * KSUB, k * KSUB, ex};
+    const size_t smem = (size_t)(TC_M + TC_N) * ix.ks * 2;
+    BPQ_CUDA(cudaFuncSetAttribute(tc_table_kernel<MODE_LUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(1, ty, M);
+    tc_table_kernel<MODE_LUT><<<grid, 128, smem, st>>>(q, D, (int)nq, pp);
     check_launch("pq table kernel");
   }
 }
@@ -202,6 +349,34 @@ void build_fbpq_tables(bpq_index& ix, cudaStream_t st) {
   cross_table_kernel<<<blocks, 256, 0, st>>>(ix.C2.as<float>(), ix.R.as<float>(), T, ix.m2, ix.s, ix.h,
                                              ix.m2, ix.X2.as<float>());
   check_launch("fbpq cross table kernel");
+  // tensor-core operands of the query tables
+  ix.kh = (ix.h + 15) & ~15;
+  ix.ks = (ix.s + 15) & ~15;
+  BPQ_CHECK(ix.kh <= 64 && ix.ks <= 64 && (ix.kh & (ix.kh - 1)) == 0 && (ix.ks & (ix.ks - 1)) == 0, BPQ_EINVAL,
+            "table operand widths must be powers of two up to 64");
+  const int64_t nR = (int64_t)ix.p.M * KSUB;
+  ix.C1b.alloc((size_t)T * ix.kh * 2);
+  ix.C2b.alloc((size_t)T * ix.kh * 2);
+  ix.Rb.alloc((size_t)nR * ix.ks * 2);
+  ix.n1.alloc((size_t)T * 4);
+  ix.n2.alloc((size_t)T * 4);
+  ix.nR.alloc((size_t)nR * 4);
+  DevBuf flags;
+  flags.alloc(8);
+  BPQ_CUDA(cudaMemsetAsync(flags.p, 0, 8, st));
+  int* fl = flags.as<int>();
+  bf16_rows_kernel<<<(T + 255) / 256, 256, 0, st>>>(ix.C1.as<float>(), T, ix.h, ix.kh, ix.C1b.as<__nv_bfloat16>(),
+                                                    ix.n1.as<float>(), fl);
+  bf16_rows_kernel<<<(T + 255) / 256, 256, 0, st>>>(ix.C2.as<float>(), T, ix.h, ix.kh, ix.C2b.as<__nv_bfloat16>(),
+                                                    ix.n2.as<float>(), fl);
+  bf16_rows_kernel<<<(int)((nR + 255) / 256), 256, 0, st>>>(ix.R.as<float>(), nR, ix.s, ix.ks,
+                                                            ix.Rb.as<__nv_bfloat16>(), ix.nR.as<float>(), fl + 1);
+  check_launch("table operand kernel");
+  int h_fl[2] = {1, 1};
+  BPQ_CUDA(cudaMemcpyAsync(h_fl, fl, 8, cudaMemcpyDeviceToHost, st));
+  BPQ_CUDA(cudaStreamSynchronize(st));
+  ix.coarse_bf16_exact = h_fl[0] == 0;
+  ix.R_bf16_exact = h_fl[1] == 0;
 }
 
 }  // namespace bpq

@@ -248,7 +248,14 @@ __device__ void block_radix_sort(uint32_t* k, uint16_t* v, uint32_t* k2, uint16_
 // Columns v < P2 of a row with distance a whose key is <= h, knowing that the
 // first `from` qualify.
 __device__ __forceinline__ int row_count(const float* s2, int P2, float a, int from, uint32_t h) {
-  int lo = from, hi = P2;  // first v with key > h lies in [lo, hi]
+  // galloping from `from` (a band moves most rows by a few columns), then bisection
+  int lo = from, hi = from, step = 1;
+  while (hi < P2 && f2ord(__fadd_rn(a, s2[hi])) <= h) {
+    lo = hi + 1;
+    hi = lo + step;
+    step <<= 1;
+  }
+  hi = min(hi, P2);  // first v with key > h lies in [lo, hi]
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
     if (f2ord(__fadd_rn(a, s2[mid])) <= h)

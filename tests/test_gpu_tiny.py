@@ -93,6 +93,41 @@ def test_query_tables_bit_exact(gpu, tiny_oracle):
         assert np.array_equal(lut[n], ref)
 
 
+def test_query_tables_all_query_counts(gpu, tiny_oracle):
+    """Tile edges of the tensor-core table kernel (128 queries per tile): 1, 127,
+    129 and 100 queries give the same rows as the full batch."""
+    full = [t.cpu().numpy() for t in gpu["ix"].query_tables(gpu["q"])]
+    q = torch.cat([gpu["q"], gpu["q"], gpu["q"]])[:300]
+    for n in (1, 127, 129, 300):
+        part = [t.cpu().numpy() for t in gpu["ix"].query_tables(q[:n].contiguous())]
+        for a, b in zip(full, part):
+            m = min(n, 100)
+            assert np.array_equal(a[:m], b[:m])
+
+
+def test_query_tables_fp32_path_for_non_bf16_inputs(gpu, tiny_oracle):
+    """Queries (or codebooks) that BF16 cannot hold exactly are tabulated in FP32
+    on the CUDA cores: within FP32 rounding of the FP64 definition."""
+    import paper_1404_1831_gb300 as bpq
+    cb = tiny_oracle["cb"]
+    s = cb.sub
+    qh = tiny_oracle["queries"][:12].astype(np.float64) + 0.25
+    d1, d2, lut = [t.cpu().numpy().astype(np.float64) for t in
+                   gpu["ix"].query_tables(torch.as_tensor(qh, dtype=torch.float32, device=DEV))]
+    for n, q in enumerate(qh):
+        o1, o2 = O.coarse_distances(q, cb)
+        assert np.allclose(d1[n], o1, rtol=1e-6, atol=1e-2) and np.allclose(d2[n], o2, rtol=1e-6, atol=1e-2)
+        ref = np.stack([(cb.R[k] ** 2).sum(1) - 2.0 * (cb.R[k] @ q[k * s:(k + 1) * s]) for k in range(cb.M)])
+        assert np.allclose(lut[n], ref, rtol=1e-6, atol=1e-1)
+    C1 = cb.C1.astype(np.float64) + 0.5  # not BF16-exact at these magnitudes
+    ix = bpq.Index.create(C1, cb.C2, cb.R)
+    d1, _, _ = [t.cpu().numpy().astype(np.float64) for t in ix.query_tables(gpu["q"][:8])]
+    for n in range(8):
+        q = tiny_oracle["queries"][n].astype(np.float64)
+        ref = ((q[None, :cb.D // 2] - C1) ** 2).sum(1)
+        assert np.allclose(d1[n], ref, rtol=1e-6, atol=1e-2)
+
+
 @pytest.mark.parametrize("L", [1, 37, 1000, 10_000, 60_000, 250_000])
 def test_traversal_bit_exact(gpu, tiny_oracle, L):
     cb, lists = tiny_oracle["cb"], tiny_oracle["index"].lists
