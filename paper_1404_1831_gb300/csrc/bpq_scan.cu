@@ -21,6 +21,7 @@
 // (the smallest k-th best of any warp) filters candidates; ids are read only for
 // candidates that pass it.  At the end the warp lists are merged by rank.
 #include <algorithm>
+#include <type_traits>
 
 #include "bpq_internal.cuh"
 
@@ -164,9 +165,9 @@ __device__ int block_excl_scan(int x, int* tmp, int* total) {
 // The buffer therefore always holds every candidate that can still be in the
 // top k (ties at v_k included); the final list is its exact (distance, id) sort.
 // ---------------------------------------------------------------------------
-template <int NT>
+template <int NT, int CAP_ = 2048>
 struct BlockTopK {
-  static constexpr int CAP = 2048;  // buffer entries; rounds add at most NT * ILP
+  static constexpr int CAP = CAP_;  // buffer entries (a power of two); rounds add at most NT * ILP
   uint64_t* buf;    // CAP
   uint64_t* alt;    // CAP (compaction target)
   int* nbuf;        // shared counter
@@ -225,8 +226,8 @@ __device__ uint32_t select_kth_hi(const uint64_t* buf, int n, int k, uint32_t* h
 
 // Keep the entries whose distance bits are <= v (the k-th smallest): moves them
 // to alt, swaps buffers.  Updates *nbuf and the threshold.
-template <int NT>
-__device__ void block_topk_prune(BlockTopK<NT>& tk, int k) {
+template <int NT, int CAP>
+__device__ void block_topk_prune(BlockTopK<NT, CAP>& tk, int k) {
   const int n = *tk.nbuf;
   if (n <= k) {
     __syncthreads();
@@ -244,7 +245,7 @@ __device__ void block_topk_prune(BlockTopK<NT>& tk, int k) {
   uint64_t* t = tk.buf;
   tk.buf = tk.alt;
   tk.alt = t;
-  if (kept > BlockTopK<NT>::CAP / 2) {
+  if (kept > CAP / 2) {
     // a huge tie group at v: sort exactly and keep k
     int n2 = 1;
     while (n2 < kept) n2 <<= 1;
@@ -262,9 +263,9 @@ __device__ void block_topk_prune(BlockTopK<NT>& tk, int k) {
 }
 
 // Final, raw: the first k composites of the exact order (EMPTY padded).
-template <int NT>
-__device__ void block_topk_finish_raw(BlockTopK<NT>& tk, int k, uint64_t* out) {
-  block_topk_prune<NT>(tk, k);
+template <int NT, int CAP>
+__device__ void block_topk_finish_raw(BlockTopK<NT, CAP>& tk, int k, uint64_t* out) {
+  block_topk_prune<NT, CAP>(tk, k);
   const int n = *tk.nbuf;
   int n2 = 1;
   while (n2 < n) n2 <<= 1;
@@ -274,9 +275,9 @@ __device__ void block_topk_finish_raw(BlockTopK<NT>& tk, int k, uint64_t* out) {
 }
 
 // Final: exact (distance, id) order of the buffer, first k written out.
-template <int NT>
-__device__ void block_topk_finish(BlockTopK<NT>& tk, int k, int32_t* out_ids, float* out_dists) {
-  block_topk_prune<NT>(tk, k);
+template <int NT, int CAP>
+__device__ void block_topk_finish(BlockTopK<NT, CAP>& tk, int k, int32_t* out_ids, float* out_dists) {
+  block_topk_prune<NT, CAP>(tk, k);
   const int n = *tk.nbuf;
   int n2 = 1;
   while (n2 < n) n2 <<= 1;
@@ -298,20 +299,46 @@ __device__ void block_topk_finish(BlockTopK<NT>& tk, int k, int32_t* out_ids, fl
 // ---------------------------------------------------------------------------
 enum { FB_POINT = 0, FB_TABLES = 1, FB_Q8 = 2 };
 
-template <int M, int VAR>
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src),
+                 "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Code words of one point as a single vector (M bytes).
+template <int M>
+using CodeVec = typename std::conditional<M == 16, uint4, uint2>::type;
+
+//  Loads are pipelined: each thread copies the codes (and cross terms) of its
+//  next round of ILP candidates into its own shared-memory slots with cp.async
+//  while it scores the current round (two slot sets), so no register holds a
+//  load in flight.
+template <int M, int VAR, int ILP, int CAP, int SUB>
 __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
   constexpr bool POINT = VAR != FB_TABLES, Q8 = VAR == FB_Q8;
-  constexpr int NT = 256, NW = NT / 32, CH = NT, ILP = 4, M2 = M / 2;
-  constexpr int SUB = 4096;          // candidates per cell-map refresh
-  constexpr int PER = SUB / NT;      // candidates per thread in the map
-  using TK = BlockTopK<NT>;
+  constexpr int NT = 256, NW = NT / 32, CH = NT, M2 = M / 2;
+  constexpr int PER = SUB / NT;      // candidates per thread in the cell map of a slice
+  using TK = BlockTopK<NT, CAP>;
+  using CV = CodeVec<M>;
   extern __shared__ __align__(16) unsigned char smem[];
   float* lut = reinterpret_cast<float*>(smem);
   uint64_t* bufs = reinterpret_cast<uint64_t*>(lut + M * KSUB);  // 2 x CAP
-  uint8_t* cmap = reinterpret_cast<uint8_t*>(bufs + 2 * TK::CAP);  // SUB
+  CV* sc = reinterpret_cast<CV*>(bufs + 2 * CAP);                 // [2][ILP][NT] staged codes
+  float* sx = reinterpret_cast<float*>(sc + 2 * ILP * NT);        // [2][ILP][NT] staged cross terms
+  uint8_t* cmap = reinterpret_cast<uint8_t*>(sx + (POINT ? 2 * ILP * NT : 0));  // SUB
   __shared__ uint32_t c_beg[CH];
-  __shared__ uint32_t c_x1[CH];
-  __shared__ uint32_t c_x2[CH];
+  __shared__ uint32_t c_x1[POINT ? 1 : CH];
+  __shared__ uint32_t c_x2[POINT ? 1 : CH];
   __shared__ float c_key[CH];
   __shared__ int c_pref[CH + 1];
   __shared__ int scan_tmp[NW + 1];
@@ -376,6 +403,25 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
         }
         __syncthreads();
         const int Pe = min(P, sub + SUB);
+        uint32_t pos_n[ILP];
+        int cid_n[ILP];
+        auto issue = [&](int b, int stg) {
+#pragma unroll
+          for (int u = 0; u < ILP; ++u) {
+            const int f = b + u * NT + threadIdx.x;
+            cid_n[u] = -1;
+            if (f < Pe) {
+              const int c = cmap[f - sub];
+              cid_n[u] = c;
+              pos_n[u] = c_beg[c] + (uint32_t)(f - c_pref[c]);
+              cp_async<sizeof(CV)>(sc + (stg * ILP + u) * NT + threadIdx.x, a.codes + (size_t)pos_n[u] * M);
+              if (POINT) cp_async<4>(sx + (stg * ILP + u) * NT + threadIdx.x, a.cross + pos_n[u]);
+            }
+          }
+          cp_async_commit();
+        };
+        int stage = 0;
+        issue(sub, 0);
         for (int base = sub; base < Pe; base += NT * ILP) {
           Code<M> code[ILP];
           float pc[ILP];
@@ -383,16 +429,32 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
           uint32_t pos[ILP];
 #pragma unroll
           for (int u = 0; u < ILP; ++u) {
-            const int f = base + u * NT + threadIdx.x;
-            cidx[u] = -1;
-            if (f < Pe) {
-              const int c = cmap[f - sub];
-              cidx[u] = c;
-              pos[u] = c_beg[c] + (uint32_t)(f - c_pref[c]);
-              code[u].load(a.codes, pos[u]);
-              if (POINT) pc[u] = __ldg(a.cross + pos[u]);
+            cidx[u] = cid_n[u];
+            pos[u] = pos_n[u];
+          }
+          if (base + NT * ILP < Pe) {
+            issue(base + NT * ILP, stage ^ 1);
+            cp_async_wait<1>();
+          } else {
+            cp_async_wait<0>();
+          }
+#pragma unroll
+          for (int u = 0; u < ILP; ++u) {
+            if (cidx[u] >= 0) {
+              const CV v = sc[(stage * ILP + u) * NT + threadIdx.x];
+              if constexpr (M == 16) {
+                code[u].w[0] = v.x;
+                code[u].w[1] = v.y;
+                code[u].w[2] = v.z;
+                code[u].w[3] = v.w;
+              } else {
+                code[u].w[0] = v.x;
+                code[u].w[1] = v.y;
+              }
+              if (POINT) pc[u] = sx[(stage * ILP + u) * NT + threadIdx.x];
             }
           }
+          stage ^= 1;
           const unsigned long long th = *(volatile unsigned long long*)&thr;
           const uint32_t th_hi = (uint32_t)(th >> 32);
 #pragma unroll
@@ -438,15 +500,15 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
             }
           }
           __syncthreads();
-          if (nbuf > TK::CAP - NT * ILP) block_topk_prune<NT>(tk, k);
+          if (nbuf > CAP - NT * ILP) block_topk_prune<NT, CAP>(tk, k);
         }
         __syncthreads();
       }
     }
     if (Q8)
-      block_topk_finish_raw<NT>(tk, k, a.sl_out + q * k);
+      block_topk_finish_raw<NT, CAP>(tk, k, a.sl_out + q * k);
     else
-      block_topk_finish<NT>(tk, k, a.out_ids + q * k, a.out_dists + q * k);
+      block_topk_finish<NT, CAP>(tk, k, a.out_ids + q * k, a.out_dists + q * k);
   }
 }
 
@@ -624,14 +686,26 @@ __global__ void __launch_bounds__(NW * 32) recon_scan_kernel(ScanArgs a) {
   }
 }
 
-template <int M, int VAR>
-void run_fbpq(const ScanArgs& a, cudaStream_t st) {
-  const size_t smem = (size_t)M * KSUB * 4 + (size_t)2 * BlockTopK<256>::CAP * 8 + 4096;
-  auto kern = fbpq_scan_kernel<M, VAR>;
+template <int M, int VAR, int ILP, int CAP, int SUB>
+void run_fbpq_cfg(const ScanArgs& a, cudaStream_t st) {
+  constexpr bool POINT = VAR != FB_TABLES;
+  const size_t smem = (size_t)M * KSUB * 4 + (size_t)2 * CAP * 8 + (size_t)2 * ILP * 256 * sizeof(CodeVec<M>) +
+                      (POINT ? (size_t)2 * ILP * 256 * 4 : 0) + SUB;
+  auto kern = fbpq_scan_kernel<M, VAR, ILP, CAP, SUB>;
   BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
   kern<<<grid, 256, smem, st>>>(a);
   check_launch("fbpq scan kernel");
+}
+
+// k <= 128: two candidates per thread per round and a 1024-entry top-k buffer
+// (small shared memory, more CTAs per SM); larger k: four and 2048.
+template <int M, int VAR>
+void run_fbpq(const ScanArgs& a, cudaStream_t st) {
+  if (a.k <= 128)
+    run_fbpq_cfg<M, VAR, 2, 1024, 2048>(a, st);
+  else
+    run_fbpq_cfg<M, VAR, 4, 2048, 4096>(a, st);
 }
 
 template <int M, int SUB, int KP, bool LOCAL>
