@@ -813,8 +813,8 @@ __device__ __forceinline__ V warp_excl_scan(V x, V* total) {
 
 // Builds the row x column grid for about `want` rows and columns.  Returns false
 // if it would exceed the caps.
-__device__ bool build_grid(WarpSmem& W, const float* d1, const float* d2, int T, int TP, float want, float min1,
-                           float min2, int* P2out, int* Rout, uint32_t* limit) {
+__device__ __noinline__ bool build_grid(WarpSmem& W, const float* d1, const float* d2, int T, int TP, float want,
+                                        float min1, float min2, int* P2out, int* Rout, uint32_t* limit) {
   const int lane = threadIdx.x & 31;
   uint32_t th1 = ORD_INF, th2 = ORD_INF;
   if (T > PCAP) {  // thresholds: a quantile of 64 sampled rows / columns each
@@ -863,7 +863,12 @@ __device__ bool build_grid(WarpSmem& W, const float* d1, const float* d2, int T,
   }
   if (P2 > PCAP || R > RCAP) return false;
   __syncwarp();
-  warp_sort_buf(W.band, P2);
+  {  // bitonic sort in shared memory (a loop: small code) over the next power of two
+    int n2 = 64;
+    while (n2 < P2) n2 <<= 1;
+    for (int v = P2 + lane; v < n2; v += 32) W.band[v] = ~0ull;
+    warp_bitonic_sort(W.band, n2);
+  }
   __syncwarp();
   for (int v = lane; v < P2; v += 32) {
     const uint64_t e = W.band[v];
@@ -1046,16 +1051,20 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
         x[i] = e < E ? W.band[e] : ~0ull;
       }
       const long long need = L - committed;
-      bool sorted = false;
-      if (a.ordered) {
-        warp_sort<8>(x);
-        sorted = true;
-      }
       load_counts();
       long long band_pts = warp_sum(mysum);
-      if (!sorted && band_pts >= need) {
-        // the last band: its cut needs the (key, cell id) order
-        warp_sort<8>(x);
+      if (a.ordered || band_pts >= need) {
+        // the visit order, or the last band (its cut needs the (key, cell id) order):
+        // bitonic sort of the band in shared memory (a loop: small code)
+        int n2 = 64;
+        while (n2 < E) n2 <<= 1;
+        for (int v = E + lane; v < n2; v += 32) W.band[v] = ~0ull;
+        warp_bitonic_sort(W.band, n2);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int e = lane * 8 + i;
+          x[i] = e < E ? W.band[e] : ~0ull;
+        }
         load_counts();
       }
       long long dummy;

@@ -87,6 +87,24 @@ def test_full_search_sampled(full, L):
     assert exact == len(SAMPLE)  # integer data: FP32 sums are exact
 
 
+@pytest.mark.parametrize("L", [10_000, 100_000])
+def test_full_traversal_sampled(full, L):
+    """The visit order (the warp pass and the CTA fallback pass) equals the full sort of
+    the T^2 cells restricted to non-empty cells, on sampled queries."""
+    from oracle import bpq_oracle as O
+    from tests.parity import cells_from_gpu
+    index = full["index"]
+    counts = index.lists.counts()
+    cap = int(min(L, (counts > 0).sum()))
+    cells, ncells, npoints = full["ix"].traverse(full["q"], L, cap)
+    got = cells_from_gpu(cells.cpu().numpy(), ncells.cpu().numpy())
+    npoints = npoints.cpu().numpy()
+    for n in SAMPLE:
+        d1, d2 = O.coarse_distances(full["qh"][n], index.cb)
+        oc, _, total = O.traverse_full_sort(d1, d2, counts, L)
+        assert np.array_equal(got[n][0], oc[counts[oc] > 0]) and npoints[n] == total
+
+
 def test_full_reconstruction_and_table_scorers_agree(full):
     """The three scorers return the same lists at the benchmark's size (Eq. 8 vs Eq. 9)."""
     a = [t.cpu().numpy() for t in full["ix"].search(full["q"], 10_000, 100, "fbpq")]
