@@ -519,18 +519,18 @@ __global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a, int onl
       }
       __syncthreads();
       const int na = na_s;
-      // warp 0: the band's upper key
-      if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+      // the band's upper key: every thread takes part in the counts (block sums),
+      // so every thread follows the same search
+      {
         auto count = [&](uint32_t h) -> long long {
           long long c = 0;
-          for (int i = lane; i < na; i += 32) {
+          for (int i = threadIdx.x; i < na; i += NT) {
             if (afk[i] <= h) {
               const int u = arow[i], v = vlo[u];
               c += row_count(s2, P2, s1[u], v + 1, h) - v;
             }
           }
-          return warp_sum(c);
+          return block_sum(c, red);
         };
         const long long cap = ECAP;
         const long long lo_ok = max(1, target / 2), hi_ok = min(cap, 2LL * target);
@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a, int onl
           }
           h = lo;
         }
-        if (lane == 0) {
+        if (threadIdx.x == 0) {
           h_s = h;
           ovf_s = ovf ? 1u : 0u;
         }
