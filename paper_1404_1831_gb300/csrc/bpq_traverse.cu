@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a, int onl
   __shared__ Red red;
   __shared__ int nband_s, nout_s, na_s, cnt_s;
   __shared__ long long emit_pts_s;
-  __shared__ uint32_t h_s, theta_s, ovf_s;
+  __shared__ uint32_t theta_s, ovf_s;
   __shared__ unsigned long long hist[258];
   const float rho = a.rho;
   const int T = a.T;
@@ -463,6 +463,8 @@ __global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a, int onl
     int nout = 0;
     bool overflow = false;
     int target = (int)fminf((float)ECAP, fmaxf(32.f, ceilf((float)L / fmaxf(rho, 1.f))));
+    float pspan = 0.f;  // key span and cells of the previous band (the band-edge model)
+    long long pcnt = 0;
     bool done = false;
     while (!done) {
       // 2. the smallest frontier key and its row
@@ -519,85 +521,112 @@ __global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a, int onl
       }
       __syncthreads();
       const int na = na_s;
-      // the band's upper key: every thread takes part in the counts (block sums),
-      // so every thread follows the same search
+      // the band's upper key h, searched by counts of the cells with key in
+      // (vlo, h].  Every thread takes part in the counts (block sums) and follows
+      // the same search.  Per compacted row, Lp holds the first column whose key
+      // exceeds lo (exact once lo is counted) and Hp the first whose key exceeds
+      // hi (P2 while hi is not counted), so a count searches each row only
+      // between the two; a thread keeps the same rows throughout, so no barrier
+      // guards them.  They live in the union region, free until the band is
+      // enumerated.
+      uint16_t* Lp = reinterpret_cast<uint16_t*>(smem);
+      uint16_t* Hp = Lp + TP;
+      uint16_t* Tp = Hp + TP;
+      for (int i = threadIdx.x; i < na; i += NT) {
+        Lp[i] = vlo[arow[i]];
+        Hp[i] = (uint16_t)P2;
+      }
       {
-        auto count = [&](uint32_t h) -> long long {
+        auto count = [&](uint32_t h) -> long long {  // per-row results go to Tp
           long long c = 0;
           for (int i = threadIdx.x; i < na; i += NT) {
-            if (afk[i] <= h) {
-              const int u = arow[i], v = vlo[u];
-              c += row_count(s2, P2, s1[u], v + 1, h) - v;
-            }
+            const int u = arow[i], v = vlo[u];
+            int r = v;
+            if (afk[i] <= h) r = row_count(s2, Hp[i], s1[u], max((int)Lp[i], v + 1), h);
+            Tp[i] = (uint16_t)r;
+            c += r - v;
           }
           return block_sum(c, red);
         };
+        auto take_lo = [&]() {
+          uint16_t* t = Lp;
+          Lp = Tp;
+          Tp = t;
+        };
+        auto take_hi = [&]() {
+          uint16_t* t = Hp;
+          Hp = Tp;
+          Tp = t;
+        };
         const long long cap = ECAP;
         const long long lo_ok = max(1, target / 2), hi_ok = min(cap, 2LL * target);
-        uint32_t h = 0;
-        bool ovf = false;
-        const long long cmin = count(hmin);
-        if (cmin > cap) {
-          ovf = true;  // one tie group larger than the band
-        } else {
-          uint32_t lo = hmin, hi = g_hi;
-          long long clo = cmin, chi = -1;
-          const long long c1 = (g1 > hmin) ? count(g1) : cmin;
-          if (c1 <= hi_ok) {
-            lo = g1;
-            clo = c1;
-          } else {
-            hi = g1;
-            chi = c1;
-          }
-          if (chi < 0) {
-            chi = (g_hi > lo) ? count(g_hi) : clo;
-            if (chi <= hi_ok) {  // the whole guess fits: take it
-              lo = g_hi;
-              clo = chi;
-            }
-          }
-          int it = 0;
-          while (hi > lo + 1 && clo < lo_ok && chi > hi_ok) {
-            uint32_t mid;
-            if (it < 8) {
-              const float flo = ord2f(lo), fhi = ord2f(hi);
-              const float sl = sqrtf((float)clo), sh = sqrtf((float)chi), sa = sqrtf(1.2f * (float)target);
-              const float frac = fminf(fmaxf((sa - sl) / fmaxf(sh - sl, 1e-6f), 0.02f), 0.98f);
-              mid = f2ord(flo + frac * (fhi - flo));
-              if (mid <= lo) mid = lo + 1;
-              if (mid >= hi) mid = hi - 1;
-            } else {
-              mid = lo + ((hi - lo) >> 1);
-            }
-            ++it;
+        // aim a little above the middle of [lo_ok, hi_ok] (larger bands, fewer passes)
+        const float aim = 1.2f * sqrtf((float)lo_ok * (float)hi_ok);
+        const float fmin = ord2f(hmin);
+        // The first band grows from a corner of the grid, so its cell count grows
+        // about quadratically with the key; later bands are strips along the
+        // frontier, which grow about linearly.  Guesses follow that model: the
+        // first from g1, later ones from the previous band's cells per key unit.
+        const bool quad = !(pspan > 0.f && pcnt > 0);
+        uint32_t lo = hmin, hi = g_hi;  // hi = g_hi is not counted until chi >= 0
+        long long clo = -1, chi = -1;   // -1: not counted (the model takes 0 at hmin)
+        if (g_hi > hmin) {
+          uint32_t mid = quad ? g1 : f2ord(fmin + pspan * (aim / (float)pcnt));
+          mid = min(g_hi, max(hmin + 1, mid));
+          for (int it = 0; it < 64; ++it) {
             const long long c = count(mid);
             if (c <= hi_ok) {
               lo = mid;
               clo = c;
+              take_lo();
+              if (c >= lo_ok || (mid == g_hi && chi < 0)) break;  // in the window, or all of g_hi fits
             } else {
               hi = mid;
               chi = c;
+              take_hi();
             }
+            if (hi <= lo + 1) break;
+            const float flo = ord2f(lo), fhi = ord2f(hi), cl = (float)max(clo, 0LL);
+            float f;
+            if (chi < 0) {  // only the lower side counted: extrapolate from hmin
+              const float r = aim / fmaxf(cl, 1.f);
+              f = fmin + (flo - fmin) * (quad ? sqrtf(r) : r);
+            } else if (it < 6) {  // interpolate inside the bracket
+              const float ch = (float)chi;
+              const float t = quad ? (sqrtf(aim) - sqrtf(cl)) / fmaxf(sqrtf(ch) - sqrtf(cl), 1e-6f)
+                                   : (aim - cl) / fmaxf(ch - cl, 1.f);
+              f = flo + (fhi - flo) * fminf(fmaxf(t, 0.05f), 0.95f);
+            } else {
+              f = -1.f;  // bisection below
+            }
+            if (f >= 0.f) {
+              mid = f2ord(f);
+            } else {
+              mid = lo + ((hi - lo) >> 1);
+            }
+            mid = max(lo + 1, mid);
+            mid = (chi < 0) ? min(hi, mid) : min(hi - 1, mid);
           }
-          h = lo;
         }
-        if (threadIdx.x == 0) {
-          h_s = h;
-          ovf_s = ovf ? 1u : 0u;
+        // nothing above hmin was counted as fitting: the band is hmin's tie
+        // group, unless that alone overflows the band capacity
+        bool ovf = false;
+        if (clo < 0) {
+          clo = count(hmin);
+          take_lo();
+          ovf = clo > cap;
         }
+        if (threadIdx.x == 0) ovf_s = ovf ? 1u : 0u;
+        pspan = ord2f(lo) - fmin;
+        pcnt = clo;
       }
       __syncthreads();
       if (ovf_s) {
         overflow = true;
         break;
       }
-      const uint32_t h = h_s;
-      // 3. enumerate the band over the compacted rows
-      for (int i = threadIdx.x; i < na; i += NT) {
-        const int u = arow[i], v = vlo[u];
-        vhic[i] = (uint16_t)((afk[i] <= h) ? row_count(s2, P2, s1[u], v + 1, h) : v);
-      }
+      // 3. enumerate the band over the compacted rows (each row ends at its Lp)
+      for (int i = threadIdx.x; i < na; i += NT) vhic[i] = Lp[i];
       __syncthreads();
       {  // exclusive prefix of the band lengths over the compacted rows
         const int per = (na + NT - 1) / NT;
