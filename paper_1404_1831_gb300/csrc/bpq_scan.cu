@@ -513,6 +513,380 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// FBPQ scan, warp-segment form (per-point cross terms, k <= 128).
+//
+// One CTA per query.  The query's cells are taken in chunks of CH; the
+// candidates of a chunk (the concatenation of its cells' list ranges) are split
+// into NW contiguous segments, one per warp.  A warp walks its segment 32
+// consecutive candidates per step: the cells of the step's 32 candidates come
+// from one OR-reduction of the cell boundaries that fall inside the step's
+// window, and the codes and cross terms of a step are loaded D steps ahead into
+// registers (coalesced: consecutive candidates of a cell are consecutive list
+// positions).
+//
+// Top-k: a candidate whose distance passes the block threshold goes to its
+// warp's buffer as (ord(distance) << 32 | list position).  A full buffer is cut
+// by a warp radix select to the entries with distance <= its k-th smallest
+// distance v, and the block threshold drops to min(threshold, v): every warp's
+// v bounds the k-th best distance of the whole query, and ties at v stay
+// accepted.  Ids are read only at the end, for the survivors, which are ranked
+// exactly by (distance, id).
+// ---------------------------------------------------------------------------
+constexpr uint32_t NO_POS = 0xffffffffu;
+
+// A cut value v for a warp buffer of n entries (k < n <= 256): at least k
+// entries have distance bits <= v, and no more than k + 32 unless the bisection
+// reaches the exact k-th smallest value first.  Bisection on the distance bits,
+// counting with each lane's eight keys held in registers.
+__device__ uint32_t warp_cut(const uint64_t* wb, int n, int k) {
+  const int lane = threadIdx.x & 31;
+  uint32_t h[8];
+  uint32_t mn = 0xffffffffu, mx = 0u;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int e = lane + 32 * i;
+    h[i] = 0xffffffffu;
+    if (e < n) {
+      h[i] = (uint32_t)(wb[e] >> 32);
+      mn = min(mn, h[i]);
+      mx = max(mx, h[i]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  // count(<= hi) >= k; count(<= lo) < k (lo = mn - 1 as a 64-bit value)
+  long long lo = (long long)mn - 1, hi = mx;
+  while (hi - lo > 1) {
+    const uint32_t mid = (uint32_t)(lo + ((hi - lo) >> 1));
+    int c = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c += (h[i] <= mid) ? 1 : 0;
+    c = warp_sum(c);
+    if (c >= k) {
+      hi = mid;
+      if (c <= k + 32) break;
+    } else {
+      lo = mid;
+    }
+  }
+  return (uint32_t)hi;
+}
+
+// Warp-wide bitonic sort (ascending) of n = power of two 64-bit keys with 32-bit
+// payloads in shared memory.
+__device__ void warp_bitonic_sort_kv(uint64_t* a, uint32_t* p, int n) {
+  const int lane = threadIdx.x & 31;
+  for (int size = 2; size <= n; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncwarp();
+      for (int t = lane; t < (n >> 1); t += 32) {
+        const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const uint64_t x = a[lo], y = a[hi];
+        if ((x > y) == up) {
+          a[lo] = y;
+          a[hi] = x;
+          const uint32_t u = p[lo];
+          p[lo] = p[hi];
+          p[hi] = u;
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// Cuts a full warp buffer (n entries, k < n <= KW) to the entries with distance
+// <= the k-th smallest distance v and lowers the block threshold to v.  If ties
+// at v keep more than half the buffer, the buffer is ranked exactly by
+// (distance, id) and cut to k.  Returns the new count.
+template <int KW>
+__device__ int warp_prune(uint64_t* wb, int n, int k, uint32_t* hist, unsigned long long* thr, const int32_t* ids) {
+  static_assert(KW == 256, "the cut keeps eight entries per lane");
+  const int lane = threadIdx.x & 31;
+  uint32_t v = warp_cut(wb, n, k);
+  int kept = 0;
+  for (int e0 = 0; e0 < n; e0 += 32) {
+    const int e = e0 + lane;
+    uint64_t x = 0;
+    bool keep = false;
+    if (e < n) {
+      x = wb[e];
+      keep = (uint32_t)(x >> 32) <= v;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    __syncwarp();  // this step's entries are read before any is overwritten
+    if (keep) wb[kept + __popc(m & lanemask_lt())] = x;
+    kept += __popc(m);
+  }
+  __syncwarp();
+  if (kept > KW / 2) {  // a large tie group at v: rank by (distance, id), keep k
+    for (int e = lane; e < KW; e += 32) {
+      if (e < kept) {
+        const uint64_t x = wb[e];
+        const uint32_t pos = (uint32_t)x;
+        hist[e] = pos;
+        wb[e] = (x & 0xffffffff00000000ull) | (uint32_t)__ldg(ids + pos);
+      } else {
+        wb[e] = EMPTY;
+      }
+    }
+    warp_bitonic_sort_kv(wb, hist, KW);
+    for (int e = lane; e < k; e += 32) wb[e] = (wb[e] & 0xffffffff00000000ull) | hist[e];
+    kept = k;
+    __syncwarp();
+    v = (uint32_t)(wb[k - 1] >> 32);
+  }
+  if (lane == 0) atomicMin(thr, ((unsigned long long)v << 32) | 0xffffffffull);
+  __syncwarp();
+  return kept;
+}
+
+// The block form of warp_cut over a[0..n) (k < n <= 8 * NT): at least k
+// entries have distance bits <= the result, and no more than k + 32 unless the
+// bisection reaches the exact k-th smallest value first.  `red` holds 2 * NT / 32
+// ints (alternating halves, one barrier per count).
+template <int NT>
+__device__ uint32_t block_cut(const uint64_t* a, int n, int k, int* red) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t h[8];
+  uint32_t mn = 0xffffffffu, mx = 0u;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int e = threadIdx.x + NT * i;
+    h[i] = 0xffffffffu;
+    if (e < n) {
+      h[i] = (uint32_t)(a[e] >> 32);
+      mn = min(mn, h[i]);
+      mx = max(mx, h[i]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (lane == 0) {
+    red[w] = (int)mn;
+    red[NW + w] = (int)mx;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int x = 0; x < NW; ++x) {
+    mn = min(mn, (uint32_t)red[x]);
+    mx = max(mx, (uint32_t)red[NW + x]);
+  }
+  __syncthreads();
+  long long lo = (long long)mn - 1, hi = mx;
+  int par = 0;
+  while (hi - lo > 1) {
+    const uint32_t mid = (uint32_t)(lo + ((hi - lo) >> 1));
+    int c = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c += (h[i] <= mid) ? 1 : 0;
+    c = warp_sum(c);
+    if (lane == 0) red[par * NW + w] = c;
+    __syncthreads();
+    c = 0;
+#pragma unroll
+    for (int x = 0; x < NW; ++x) c += red[par * NW + x];
+    par ^= 1;
+    if (c >= k) {
+      hi = mid;
+      if (c <= k + 32) break;
+    } else {
+      lo = mid;
+    }
+  }
+  return (uint32_t)hi;
+}
+
+template <int M, int NT, int D, int KW, int CH>
+__global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
+  constexpr int NW = NT / 32, R = CH / NT;
+  static_assert(CH % NT == 0 && KW == 256, "shape (the exact prune keeps its payloads in the warp's 256 counters)");
+  using CV = CodeVec<M>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* lut = reinterpret_cast<float*>(smem);                    // M x 256
+  uint64_t* wbuf = reinterpret_cast<uint64_t*>(lut + M * KSUB);   // NW x KW
+  uint32_t* whist = reinterpret_cast<uint32_t*>(wbuf + NW * KW);  // NW x 256
+  int2* c_info = reinterpret_cast<int2*>(whist + NW * 256);       // CH: (begin - first candidate, key bits)
+  int* c_pref = reinterpret_cast<int*>(c_info + CH);              // CH + 1: first candidate of each cell
+  __shared__ int scan_tmp[NW + 1];
+  __shared__ int cut_red[2 * NW];
+  __shared__ int fcount;
+  __shared__ unsigned long long thr;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k = a.k;
+  uint64_t* wb = wbuf + w * KW;
+  uint32_t* hist = whist + w * 256;
+  const char* lutb = reinterpret_cast<const char*>(lut);
+
+  for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
+    __syncthreads();  // the previous query's final list (in the table area) is written out
+    {
+      const float4* src = reinterpret_cast<const float4*>(a.lut + q * M * KSUB);
+      for (int t = threadIdx.x; t < M * KSUB / 4; t += NT) reinterpret_cast<float4*>(lut)[t] = src[t];
+    }
+    if (threadIdx.x == 0) thr = EMPTY;
+    int wn = 0;  // entries in this warp's buffer (uniform across the warp)
+    const int nc = max(0, a.ncells[q]);
+    const bpq_cell* cl = a.cells + q * (int64_t)a.cap;
+    for (int cs = 0; cs < nc; cs += CH) {
+      const int nch = min(CH, nc - cs);
+      // first candidate of each cell of the chunk (thread t takes cells
+      // tR .. tR + R - 1; the second read of a cell hits the cache)
+      int loc = 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int t = threadIdx.x * R + r;
+        if (t < nch) loc += (int)cl[cs + t].count;
+      }
+      __syncthreads();  // the previous chunk's cells are no longer read
+      int total;
+      int run = block_excl_scan<NT>(loc, scan_tmp, &total);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int t = threadIdx.x * R + r;
+        if (t < nch) {
+          const bpq_cell cc = cl[cs + t];
+          c_pref[t] = run;
+          c_info[t] = make_int2((int)cc.begin - run, __float_as_int(cc.key));
+          run += (int)cc.count;
+        }
+      }
+      if (threadIdx.x == 0) c_pref[nch] = total;
+      __syncthreads();
+      const int P = total;
+      const int s = (int)(((long long)P * w) / NW), e = (int)(((long long)P * (w + 1)) / NW);
+      if (s < e) {
+        int c = find_cell(c_pref, nch, s);  // cell of the next step's first candidate
+        int f = s;                          // next step's first candidate
+        uint32_t spos[D];
+        float skey[D], sx[D];
+        CV scode[D];
+        auto issue = [&](int d) {
+          spos[d] = NO_POS;
+          if (f < e) {
+            const int b = (c + 1 + lane <= nch) ? c_pref[c + 1 + lane] : 0x7fffffff;
+            const int o = b - f;  // >= 1: offset of the start of cell c + 1 + lane
+            const unsigned msk = __reduce_or_sync(0xffffffffu, o < 32 ? (1u << o) : 0u);
+            const int fl = f + lane;
+            if (fl < e) {
+              const int2 inf = c_info[c + __popc(msk & ((2u << lane) - 1u))];
+              const uint32_t pos = (uint32_t)(fl + inf.x);
+              spos[d] = pos;
+              skey[d] = __int_as_float(inf.y);
+              scode[d] = __ldg(reinterpret_cast<const CV*>(a.codes) + pos);
+              sx[d] = __ldg(a.cross + pos);
+            }
+            c += __popc(msk);
+            if (c + 1 <= nch && c_pref[c + 1] == f + 32) ++c;
+            f += 32;
+          }
+        };
+#pragma unroll
+        for (int d = 0; d < D; ++d) issue(d);
+        for (int left = (e - s + 31) >> 5; left > 0; left -= D) {
+          const uint32_t th_hi = (uint32_t)(*(volatile unsigned long long*)&thr >> 32);
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            const uint32_t pos = spos[d];
+            bool acc = false;
+            uint32_t o = 0;
+            if (pos != NO_POS) {
+              float part = sx[d];
+              uint32_t wd[M / 4];
+              if constexpr (M == 16) {
+                wd[0] = scode[d].x;
+                wd[1] = scode[d].y;
+                wd[2] = scode[d].z;
+                wd[3] = scode[d].w;
+              } else {
+                wd[0] = scode[d].x;
+                wd[1] = scode[d].y;
+              }
+#pragma unroll
+              for (int kk = 0; kk < M; ++kk) {
+                const uint32_t off = ((wd[kk >> 2] >> (8 * (kk & 3))) & 0xffu) << 2;
+                part += *reinterpret_cast<const float*>(lutb + kk * (KSUB * 4) + off);
+              }
+              o = f2ord(skey[d] + part);
+              acc = o <= th_hi;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, acc);
+            if (m) {
+              if (acc) wb[wn + __popc(m & lanemask_lt())] = ((uint64_t)o << 32) | pos;
+              wn += __popc(m);
+              if (wn > KW - 32) {
+                __syncwarp();
+                wn = warp_prune<KW>(wb, wn, k, hist, &thr, a.ids);
+              }
+            }
+            issue(d);
+          }
+        }
+      }
+    }
+    // final: the entries within the block threshold are gathered into the table
+    // area (it holds every buffer), cut near the k best distances, given their
+    // ids (read only here) and ranked exactly by (distance, id)
+    static_assert(NW * KW <= M * KSUB * 4 / 8, "the table area holds every buffered entry");
+    __syncthreads();
+    const uint32_t th_hi = (uint32_t)(thr >> 32);
+    int mine = 0;
+    for (int e0 = 0; e0 < wn; e0 += 32) {
+      const int e = e0 + lane;
+      mine += __popc(__ballot_sync(0xffffffffu, e < wn && (uint32_t)(wb[e] >> 32) <= th_hi));
+    }
+    if (lane == 0) scan_tmp[w] = mine;
+    if (threadIdx.x == 0) fcount = 0;
+    __syncthreads();
+    int base = 0, n = 0;
+#pragma unroll
+    for (int x = 0; x < NW; ++x) {
+      base += (x < w) ? scan_tmp[x] : 0;
+      n += scan_tmp[x];
+    }
+    uint64_t* fin = reinterpret_cast<uint64_t*>(lut);  // the table is no longer read
+    for (int e0 = 0; e0 < wn; e0 += 32) {
+      const int e = e0 + lane;
+      const uint64_t x = e < wn ? wb[e] : EMPTY;
+      const bool keep = e < wn && (uint32_t)(x >> 32) <= th_hi;
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (keep) fin[base + __popc(m & lanemask_lt())] = x;
+      base += __popc(m);
+    }
+    __syncthreads();
+    const uint32_t v = (n > k) ? block_cut<NT>(fin, n, k, cut_red) : 0xffffffffu;
+    for (int t = threadIdx.x; t < n; t += NT) {
+      const uint64_t x = fin[t];
+      if ((uint32_t)(x >> 32) <= v)
+        wbuf[atomicAdd(&fcount, 1)] = (x & 0xffffffff00000000ull) | (uint32_t)__ldg(a.ids + (uint32_t)x);
+    }
+    __syncthreads();
+    const int m = fcount;
+    for (int t = threadIdx.x; t < m; t += NT) {  // rank among the survivors (composites are distinct)
+      const uint64_t x = wbuf[t];
+      int r = 0;
+      for (int j = 0; j < m; ++j) r += (wbuf[j] < x) ? 1 : 0;
+      if (r < k) {
+        a.out_ids[q * k + r] = (int32_t)(uint32_t)x;
+        a.out_dists[q * k + r] = ord2f((uint32_t)(x >> 32));
+      }
+    }
+    for (int r = m + threadIdx.x; r < k; r += NT) {
+      a.out_ids[q * k + r] = -1;
+      a.out_dists[q * k + r] = __int_as_float(0x7f800000);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Exact re-score of a shortlist (bpq_search_shortlist step 3): one CTA per
 // query; each shortlisted list position finds its cell by binary search on the
 // offsets, then its FBPQ distance (Eqs. 8-9) is formed exactly as in the FP32
@@ -698,11 +1072,27 @@ void run_fbpq_cfg(const ScanArgs& a, cudaStream_t st) {
   check_launch("fbpq scan kernel");
 }
 
-// k <= 128: two candidates per thread per round and a 1024-entry top-k buffer
-// (small shared memory, more CTAs per SM); larger k: four and 2048.
+template <int M, int NT, int D, int KW, int CH>
+void run_fbpq_seg(const ScanArgs& a, cudaStream_t st) {
+  constexpr int NW = NT / 32;
+  const size_t smem = (size_t)M * KSUB * 4 + (size_t)NW * KW * 8 + (size_t)NW * 256 * 4 + (size_t)CH * 8 +
+                      (size_t)(CH + 1) * 4;
+  auto kern = fbpq_scan_seg_kernel<M, NT, D, KW, CH>;
+  BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
+  kern<<<grid, NT, smem, st>>>(a);
+  check_launch("fbpq segment scan kernel");
+}
+
+// Per-point cross terms and k <= 128: the warp-segment scan.  Otherwise the
+// round-based scan: k <= 128 with two candidates per thread per round and a
+// 1024-entry top-k buffer (small shared memory, more CTAs per SM); larger k:
+// four and 2048.
 template <int M, int VAR>
 void run_fbpq(const ScanArgs& a, cudaStream_t st) {
-  if (a.k <= 128)
+  if (VAR == FB_POINT && a.k <= 128)
+    run_fbpq_seg<M, 128, 2, 256, 512>(a, st);
+  else if (a.k <= 128)
     run_fbpq_cfg<M, VAR, 2, 1024, 2048>(a, st);
   else
     run_fbpq_cfg<M, VAR, 4, 2048, 4096>(a, st);
