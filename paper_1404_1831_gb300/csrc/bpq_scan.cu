@@ -517,12 +517,12 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
 //
 // One CTA per query.  The query's cells are taken in chunks of CH; the
 // candidates of a chunk (the concatenation of its cells' list ranges) are split
-// into NW contiguous segments, one per warp.  A warp walks its segment 32
-// consecutive candidates per step: the cells of the step's 32 candidates come
-// from one OR-reduction of the cell boundaries that fall inside the step's
-// window, and the codes and cross terms of a step are loaded D steps ahead into
-// registers (coalesced: consecutive candidates of a cell are consecutive list
-// positions).
+// into NW contiguous segments, one per warp.  A warp walks its segment 32U
+// consecutive candidates per step (U per lane): the cells of the step's
+// candidates come from OR-reductions of the cell boundaries that fall inside
+// the step's window, and the codes and cross terms of a step are loaded D steps
+// ahead into registers (coalesced: consecutive candidates of a cell are
+// consecutive list positions).
 //
 // Top-k: a candidate whose distance passes the block threshold goes to its
 // warp's buffer as (ord(distance) << 32 | list position).  A full buffer is cut
@@ -705,7 +705,7 @@ __device__ uint32_t block_cut(const uint64_t* a, int n, int k, int* red) {
   return (uint32_t)hi;
 }
 
-template <int M, int NT, int D, int KW, int CH>
+template <int M, int NT, int D, int U, int KW, int CH>
 __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
   constexpr int NW = NT / 32, R = CH / NT;
   static_assert(CH % NT == 0 && KW == 256, "shape (the exact prune keeps its payloads in the warp's 256 counters)");
@@ -766,65 +766,90 @@ __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
       if (s < e) {
         int c = find_cell(c_pref, nch, s);  // cell of the next step's first candidate
         int f = s;                          // next step's first candidate
-        uint32_t spos[D];
-        float skey[D], sx[D];
-        CV scode[D];
+        const unsigned le = (2u << lane) - 1u;
+        uint32_t spos[D][U];
+        float skey[D][U], sx[D][U];
+        CV scode[D][U];
+        // a step: candidates f + 32u + lane (u < U); the cell starts that fall in
+        // half h of the window [f, f + 32U) set bits of msk[h]
         auto issue = [&](int d) {
-          spos[d] = NO_POS;
+#pragma unroll
+          for (int u = 0; u < U; ++u) spos[d][u] = NO_POS;
           if (f < e) {
-            const int b = (c + 1 + lane <= nch) ? c_pref[c + 1 + lane] : 0x7fffffff;
-            const int o = b - f;  // >= 1: offset of the start of cell c + 1 + lane
-            const unsigned msk = __reduce_or_sync(0xffffffffu, o < 32 ? (1u << o) : 0u);
-            const int fl = f + lane;
-            if (fl < e) {
-              const int2 inf = c_info[c + __popc(msk & ((2u << lane) - 1u))];
-              const uint32_t pos = (uint32_t)(fl + inf.x);
-              spos[d] = pos;
-              skey[d] = __int_as_float(inf.y);
-              scode[d] = __ldg(reinterpret_cast<const CV*>(a.codes) + pos);
-              sx[d] = __ldg(a.cross + pos);
+            unsigned bits[U];
+#pragma unroll
+            for (int h = 0; h < U; ++h) bits[h] = 0u;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int i = c + 1 + 32 * u + lane;
+              const int o = (i <= nch ? c_pref[i] : 0x7fffffff) - f;  // >= 1 + 32u
+#pragma unroll
+              for (int h = u; h < U; ++h)
+                if (o >= 32 * h && o < 32 * h + 32) bits[h] |= 1u << (o - 32 * h);
             }
-            c += __popc(msk);
-            if (c + 1 <= nch && c_pref[c + 1] == f + 32) ++c;
-            f += 32;
+            int below = c;
+#pragma unroll
+            for (int h = 0; h < U; ++h) {
+              const unsigned msk = __reduce_or_sync(0xffffffffu, bits[h]);
+              const int fl = f + 32 * h + lane;
+              if (fl < e) {
+                const int2 inf = c_info[below + __popc(msk & le)];
+                const uint32_t pos = (uint32_t)(fl + inf.x);
+                spos[d][h] = pos;
+                skey[d][h] = __int_as_float(inf.y);
+                scode[d][h] = __ldg(reinterpret_cast<const CV*>(a.codes) + pos);
+                sx[d][h] = __ldg(a.cross + pos);
+              }
+              below += __popc(msk);
+            }
+            c = below;
+            if (c + 1 <= nch && c_pref[c + 1] == f + 32 * U) ++c;
+            f += 32 * U;
           }
         };
 #pragma unroll
         for (int d = 0; d < D; ++d) issue(d);
-        for (int left = (e - s + 31) >> 5; left > 0; left -= D) {
+        for (int left = (e - s + 32 * U - 1) / (32 * U); left > 0; left -= D) {
           const uint32_t th_hi = (uint32_t)(*(volatile unsigned long long*)&thr >> 32);
 #pragma unroll
           for (int d = 0; d < D; ++d) {
-            const uint32_t pos = spos[d];
-            bool acc = false;
-            uint32_t o = 0;
-            if (pos != NO_POS) {
-              float part = sx[d];
-              uint32_t wd[M / 4];
-              if constexpr (M == 16) {
-                wd[0] = scode[d].x;
-                wd[1] = scode[d].y;
-                wd[2] = scode[d].z;
-                wd[3] = scode[d].w;
-              } else {
-                wd[0] = scode[d].x;
-                wd[1] = scode[d].y;
-              }
+            uint32_t o[U];
+            bool acc[U];
 #pragma unroll
-              for (int kk = 0; kk < M; ++kk) {
-                const uint32_t off = ((wd[kk >> 2] >> (8 * (kk & 3))) & 0xffu) << 2;
-                part += *reinterpret_cast<const float*>(lutb + kk * (KSUB * 4) + off);
+            for (int u = 0; u < U; ++u) {
+              acc[u] = false;
+              o[u] = 0;
+              if (spos[d][u] != NO_POS) {
+                float part = sx[d][u];
+                uint32_t wd[M / 4];
+                if constexpr (M == 16) {
+                  wd[0] = scode[d][u].x;
+                  wd[1] = scode[d][u].y;
+                  wd[2] = scode[d][u].z;
+                  wd[3] = scode[d][u].w;
+                } else {
+                  wd[0] = scode[d][u].x;
+                  wd[1] = scode[d][u].y;
+                }
+#pragma unroll
+                for (int kk = 0; kk < M; ++kk) {
+                  const uint32_t off = ((wd[kk >> 2] >> (8 * (kk & 3))) & 0xffu) << 2;
+                  part += *reinterpret_cast<const float*>(lutb + kk * (KSUB * 4) + off);
+                }
+                o[u] = f2ord(skey[d][u] + part);
+                acc[u] = o[u] <= th_hi;
               }
-              o = f2ord(skey[d] + part);
-              acc = o <= th_hi;
             }
-            const unsigned m = __ballot_sync(0xffffffffu, acc);
-            if (m) {
-              if (acc) wb[wn + __popc(m & lanemask_lt())] = ((uint64_t)o << 32) | pos;
-              wn += __popc(m);
-              if (wn > KW - 32) {
-                __syncwarp();
-                wn = warp_prune<KW>(wb, wn, k, hist, &thr, a.ids);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const unsigned m = __ballot_sync(0xffffffffu, acc[u]);
+              if (m) {
+                if (acc[u]) wb[wn + __popc(m & lanemask_lt())] = ((uint64_t)o[u] << 32) | spos[d][u];
+                wn += __popc(m);
+                if (wn > KW - 32) {
+                  __syncwarp();
+                  wn = warp_prune<KW>(wb, wn, k, hist, &thr, a.ids);
+                }
               }
             }
             issue(d);
@@ -1072,12 +1097,12 @@ void run_fbpq_cfg(const ScanArgs& a, cudaStream_t st) {
   check_launch("fbpq scan kernel");
 }
 
-template <int M, int NT, int D, int KW, int CH>
+template <int M, int NT, int D, int U, int KW, int CH>
 void run_fbpq_seg(const ScanArgs& a, cudaStream_t st) {
   constexpr int NW = NT / 32;
   const size_t smem = (size_t)M * KSUB * 4 + (size_t)NW * KW * 8 + (size_t)NW * 256 * 4 + (size_t)CH * 8 +
                       (size_t)(CH + 1) * 4;
-  auto kern = fbpq_scan_seg_kernel<M, NT, D, KW, CH>;
+  auto kern = fbpq_scan_seg_kernel<M, NT, D, U, KW, CH>;
   BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
   kern<<<grid, NT, smem, st>>>(a);
@@ -1091,7 +1116,7 @@ void run_fbpq_seg(const ScanArgs& a, cudaStream_t st) {
 template <int M, int VAR>
 void run_fbpq(const ScanArgs& a, cudaStream_t st) {
   if (VAR == FB_POINT && a.k <= 128)
-    run_fbpq_seg<M, 128, 2, 256, 512>(a, st);
+    run_fbpq_seg<M, 128, 1, 2, 256, 512>(a, st);
   else if (a.k <= 128)
     run_fbpq_cfg<M, VAR, 2, 1024, 2048>(a, st);
   else
