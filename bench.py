@@ -393,7 +393,8 @@ def run_ours(args):
     if tr:  # DRAM bytes of a smaller captured launch, scaled by the units this launch processes
         traffic = tr["bytes_per_candidate"] * cand if dominant == "scan" else tr["bytes_per_query"] * nq
     if dominant == "scan":
-        roof = {"kernel": f"{scorer}_scan_kernel", "bound": "hbm", "achieved": scan_bytes / (ph["scan"] / 1e3) / 1e9,
+        kname = "fbpq_scan_seg_kernel" if scorer == "fbpq" and k <= 128 else f"{scorer}_scan_kernel"
+        roof = {"kernel": kname, "bound": "hbm", "achieved": scan_bytes / (ph["scan"] / 1e3) / 1e9,
                 "peak": hbm_peak, "unit": "GB/s", "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": scan_bytes, "bytes_per_candidate": w.M + 4,
                 "traffic": traffic, "traffic_source": tr["source"] if tr else None}
