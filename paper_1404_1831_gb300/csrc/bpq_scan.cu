@@ -1116,7 +1116,7 @@ void run_fbpq_seg(const ScanArgs& a, cudaStream_t st) {
 template <int M, int VAR>
 void run_fbpq(const ScanArgs& a, cudaStream_t st) {
   if (VAR == FB_POINT && a.k <= 128)
-    run_fbpq_seg<M, 128, 1, 2, 256, 512>(a, st);
+    run_fbpq_seg<M, 128, 1, 4, 256, 512>(a, st);
   else if (a.k <= 128)
     run_fbpq_cfg<M, VAR, 2, 1024, 2048>(a, st);
   else
