@@ -111,3 +111,13 @@ def test_full_reconstruction_and_table_scorers_agree(full):
     for scorer in ("fbpq_tables", "recon"):
         b = [t.cpu().numpy() for t in full["ix"].search(full["q"], 10_000, 100, scorer)]
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_full_batch_equals_small_batches(full):
+    """Queries are independent (each CTA or warp owns one query): a batch of 10k gives the
+    same lists as five batches of 2000."""
+    import torch
+    a = [t.cpu().numpy() for t in full["ix"].search(full["q"], 10_000, 100, "fbpq")]
+    parts = [full["ix"].search(full["q"][i:i + 2000], 10_000, 100, "fbpq") for i in range(0, full["q"].shape[0], 2000)]
+    b = [torch.cat([p[j] for p in parts]).cpu().numpy() for j in range(2)]
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
