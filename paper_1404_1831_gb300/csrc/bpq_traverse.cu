@@ -932,6 +932,8 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
     // rows and columns for about 5 sqrt(L / rho) + 32 visited cells; a query
     // that would need more than the caps goes straight to the CTA kernel
     float want = 5.f * sqrtf((float)L / rho) + 32.f;
+    float pspan = 0.f;  // key span and cells of the previous band (the band-edge model)
+    long long pcnt = 0;
     const float want_max = 0.9f * (float)PCAP;
     if (want > want_max && T > PCAP) {
       if (lane == 0) a.ncells[q] = FALLBACK;
@@ -974,78 +976,104 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
         continue;
       }
       const int rh = (int)(uint32_t)fm;
-      auto count = [&](uint32_t h) -> long long {
+      // The band's upper key, searched by counts of the cells with key in
+      // (vlo, h] as in the CTA kernel: guesses from the band growth model, and
+      // per row the first column above lo (Lp, exact once lo is counted) and
+      // above hi (Hp; P2 while hi is not counted), kept between counts in the
+      // band buffer (free until the band is enumerated).  Lane l keeps rows
+      // l, l + 32, ... throughout, so no barrier guards them.
+      uint16_t* Lp = reinterpret_cast<uint16_t*>(W.band);
+      uint16_t* Hp = Lp + RCAP;
+      uint16_t* Tp = Hp + RCAP;
+      for (int r = lane; r < R; r += 32) {
+        Lp[r] = W.vloid[W.rid[r]];
+        Hp[r] = (uint16_t)P2;
+      }
+      auto count = [&](uint32_t h) -> long long {  // per-row results go to Tp
         long long c = 0;
         for (int r = lane; r < R; r += 32) {
-          if (W.rfk[r] <= h) {
-            const int v = W.vloid[W.rid[r]];
-            c += row_count(W.cs2, P2, W.rs1[r], v + 1, h) - v;
-          }
+          const int v = W.vloid[W.rid[r]];
+          int e = v;
+          if (W.rfk[r] <= h) e = row_count(W.cs2, Hp[r], W.rs1[r], max((int)Lp[r], v + 1), h);
+          Tp[r] = (uint16_t)e;
+          c += e - v;
         }
         return warp_sum(c);
       };
-      const long long cmin = count(hmin);
-      if (cmin > BCAP) {  // a tie group larger than a band
-        fb = true;
-        break;
-      }
+      auto take_lo = [&]() {
+        uint16_t* t = Lp;
+        Lp = Tp;
+        Tp = t;
+      };
+      auto take_hi = [&]() {
+        uint16_t* t = Hp;
+        Hp = Tp;
+        Tp = t;
+      };
       const uint32_t lim1 = limit == ORD_INF ? ORD_INF - 1 : limit - 1;
       const int vh = W.vloid[W.rid[rh]];
       const float sh = W.rs1[rh];
       const uint32_t g_hi = min(lim1, f2ord(__fadd_rn(sh, W.cs2[min(P2 - 1, vh + BCAP)])));
       const uint32_t g1 = min(g_hi, f2ord(__fadd_rn(sh, W.cs2[min(P2 - 1, vh + 16)])));
       const long long lo_ok = BCAP / 2, hi_ok = BCAP;
-      uint32_t lo = hmin, hi = g_hi;
-      long long clo = cmin, chi = -1;
-      {
-        const long long c1 = (g1 > hmin) ? count(g1) : cmin;
-        if (c1 <= hi_ok) {
-          lo = g1;
-          clo = c1;
-        } else {
-          hi = g1;
-          chi = c1;
-        }
-        if (chi < 0) {
-          chi = (g_hi > lo) ? count(g_hi) : clo;
-          if (chi <= hi_ok) {
-            lo = g_hi;
-            clo = chi;
-          }
-        }
-        int it = 0;
-        while (hi > lo + 1 && clo < lo_ok && chi > hi_ok) {
-          uint32_t mid;
-          if (it < 8) {
-            const float flo = ord2f(lo), fhi = ord2f(hi);
-            const float sl = sqrtf((float)clo), shh = sqrtf((float)chi), sa = sqrtf(0.75f * (float)BCAP);
-            const float frac = fminf(fmaxf((sa - sl) / fmaxf(shh - sl, 1e-6f), 0.02f), 0.98f);
-            mid = f2ord(flo + frac * (fhi - flo));
-            if (mid <= lo) mid = lo + 1;
-            if (mid >= hi) mid = hi - 1;
-          } else {
-            mid = lo + ((hi - lo) >> 1);
-          }
-          ++it;
+      const float aim = 1.2f * sqrtf((float)lo_ok * (float)hi_ok);
+      const float fmin = ord2f(hmin);
+      const bool quad = !(pspan > 0.f && pcnt > 0);
+      uint32_t lo = hmin, hi = g_hi;  // hi = g_hi is not counted until chi >= 0
+      long long clo = -1, chi = -1;
+      if (g_hi > hmin) {
+        uint32_t mid = quad ? g1 : f2ord(fmin + pspan * (aim / (float)pcnt));
+        mid = min(g_hi, max(hmin + 1, mid));
+        for (int it = 0; it < 64; ++it) {
           const long long c = count(mid);
           if (c <= hi_ok) {
             lo = mid;
             clo = c;
+            take_lo();
+            if (c >= lo_ok || (mid == g_hi && chi < 0)) break;  // in the window, or all of g_hi fits
           } else {
             hi = mid;
             chi = c;
+            take_hi();
           }
+          if (hi <= lo + 1) break;
+          const float flo = ord2f(lo), fhi = ord2f(hi), cl = (float)max(clo, 0LL);
+          float f;
+          if (chi < 0) {  // only the lower side counted: extrapolate from hmin
+            const float r = aim / fmaxf(cl, 1.f);
+            f = fmin + (flo - fmin) * (quad ? sqrtf(r) : r);
+          } else if (it < 6) {  // interpolate inside the bracket
+            const float ch = (float)chi;
+            const float t = quad ? (sqrtf(aim) - sqrtf(cl)) / fmaxf(sqrtf(ch) - sqrtf(cl), 1e-6f)
+                                 : (aim - cl) / fmaxf(ch - cl, 1.f);
+            f = flo + (fhi - flo) * fminf(fmaxf(t, 0.05f), 0.95f);
+          } else {
+            f = -1.f;
+          }
+          mid = (f >= 0.f) ? f2ord(f) : lo + ((hi - lo) >> 1);
+          mid = max(lo + 1, mid);
+          mid = (chi < 0) ? min(hi, mid) : min(hi - 1, mid);
         }
       }
-      const uint32_t h = lo;
-      // the band's cells: columns [vlo, vhi) of every row
+      if (clo < 0) {  // nothing above hmin fits: hmin's tie group, unless it overflows a band
+        clo = count(hmin);
+        take_lo();
+        if (clo > BCAP) {
+          fb = true;
+          break;
+        }
+      }
+      pspan = ord2f(lo) - fmin;
+      pcnt = clo;
+      // the band's cells: columns [vlo, Lp) of every row
       int loc = 0;
       for (int r = lane; r < R; r += 32) {
         const int v = W.vloid[W.rid[r]];
-        const int vhi = (W.rfk[r] <= h) ? row_count(W.cs2, P2, W.rs1[r], v + 1, h) : v;
+        const int vhi = Lp[r];
         W.rvhi[r] = (uint16_t)vhi;
         loc += vhi - v;
       }
+      __syncwarp();  // the band buffer is overwritten below
       int E;
       int pos = warp_excl_scan(loc, &E);
       for (int r = lane; r < R; r += 32) {
