@@ -440,15 +440,52 @@ def quantize_table_int8(lut):
     return q8, np.float32(step)
 
 
-def search_shortlist_one(index: OracleIndex, q, L, k, S):
-    """One query of the int8-table search: the visited cells and candidates of
-    search_one; score = (key(i,j) + cross(p)) + s * sum_k q8[k][c_k] in FP32 (the
-    constant sum_k lo_k is left out); the S best by (score, list position) are
-    re-scored with the exact FBPQ distance (Eqs. 8-9) and ranked by (distance, id).
-    Returns (ids (k,), dists (k,))."""
+FP16_MAX = 65504.0
+
+
+def quantize_table_fp16(lut):
+    """Per sub-quantizer offset lo_k = min_t lut[k][t] and one per-query step s, the
+    smallest power of two >= 1 with max_k (max_t lut[k][t] - lo_k) <= 65504 s (the
+    largest finite FP16 value), so the scaling is exact; h[k][t] = the FP16 value
+    nearest to (lut[k][t] - lo_k) / s (ties to even).  Returns (h float16 (M, 256),
+    s float32)."""
+    lut32 = np.asarray(lut, np.float64).astype(np.float32)
+    x = lut32 - lut32.min(axis=1)[:, None]
+    rng = float(x.max())
+    step = 1.0
+    while rng > FP16_MAX * step:
+        step *= 2.0
+    h = (x / np.float32(step)).astype(np.float16)
+    return h, np.float32(step)
+
+
+def shortlist_part(q, cb, codes, precision):
+    """The reduced-precision part of a shortlist score, in FP32: s * sum_k q8[k][c_k]
+    (int8: an exact integer sum) or s * (((h[0][c_0] + h[1][c_1]) + ...) + h[M-1][c_{M-1}])
+    (fp16: FP32 additions in sub-quantizer order)."""
+    lut = pq_table(q, cb)
+    cols = np.arange(cb.M)
+    if precision == "int8":
+        q8, step = quantize_table_int8(lut)
+        return step * q8[cols[None, :], codes].sum(1).astype(np.float32)
+    if precision == "fp16":
+        h, step = quantize_table_fp16(lut)
+        acc = np.zeros(len(codes), np.float32)
+        for kk in range(cb.M):
+            acc = acc + h[kk, codes[:, kk]].astype(np.float32)
+        return step * acc
+    raise ValueError(precision)
+
+
+def search_shortlist_one(index: OracleIndex, q, L, k, S, precision="int8"):
+    """One query of the reduced-precision table search: the visited cells and
+    candidates of search_one; score = (key(i,j) + cross(p)) + part in FP32, part
+    from shortlist_part (the constant sum_k lo_k is left out); the S best by
+    (score, list position) are re-scored with the exact FBPQ distance (Eqs. 8-9)
+    and ranked by (distance, id).  Returns (ids (k,), dists (k,))."""
     cb, lists, tab = index.cb, index.lists, index.tables
     if index.variant != "global":
-        raise ValueError("the int8 shortlist scores global codes")
+        raise ValueError("the reduced-precision shortlist scores global codes")
     d1, d2 = coarse_distances(q, cb)
     cells, _, _ = traverse_full_sort(d1, d2, lists.counts(), L)
     pos = candidates(cells, lists)
@@ -457,22 +494,20 @@ def search_shortlist_one(index: OracleIndex, q, L, k, S):
     i, j = cell_of // cb.T, cell_of % cb.T
     key32 = (d1[i] + d2[j]).astype(np.float32)
     cross32 = point_cross(cb, tab, cell_of, codes).astype(np.float32)
-    q8, step = quantize_table_int8(pq_table(q, cb))
-    isum = q8[np.arange(cb.M)[None, :], codes].sum(1).astype(np.float32)
-    score = (key32 + cross32) + step * isum
+    score = (key32 + cross32) + shortlist_part(q, cb, codes, precision)
     short = np.lexsort((pos, score))[:S]
     exact = dist_fbpq(q, cb, tab, cell_of[short], codes[short])
     return topk(exact, lists.ids[pos[short]], k)
 
 
-def search_shortlist(index: OracleIndex, queries, L, k, S):
+def search_shortlist(index: OracleIndex, queries, L, k, S, precision="int8"):
     queries = np.asarray(queries)
     nq = len(queries)
     Ls = np.broadcast_to(np.asarray(L, dtype=np.int64), (nq,))
     ids = np.empty((nq, k), dtype=np.int64)
     dists = np.empty((nq, k))
     for n in range(nq):
-        ids[n], dists[n] = search_shortlist_one(index, queries[n], int(Ls[n]), k, S)
+        ids[n], dists[n] = search_shortlist_one(index, queries[n], int(Ls[n]), k, S, precision)
     return ids, dists
 
 

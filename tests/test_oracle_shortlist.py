@@ -86,3 +86,58 @@ def test_short_shortlist_keeps_distances_exact(small):
         where = {int(i): float(v) for i, v in zip(full_ids, full_d)}
         assert all(where[int(i)] == float(v) for i, v in zip(ids, d) if i >= 0)
         assert np.all(np.diff(d) >= 0)
+
+
+def test_fp16_table_is_nearest_value_at_smallest_power_of_two_step(small):
+    """Every stored entry is the FP16 value nearest to (lut - lo_k) / s: neither FP16
+    neighbour is closer (checked through np.nextafter, not the conversion); s is the
+    smallest power of two >= 1 that keeps the widest table finite."""
+    for q in small["q"][:3]:
+        lut = O.pq_table(q, small["cb"])
+        h, s = O.quantize_table_fp16(lut)
+        assert h.dtype == np.float16 and np.isfinite(h).all()
+        x = (lut - lut.min(1)[:, None]) / float(s)
+        assert x.max() <= 65504.0 and (s == 1 or x.max() * 2 > 65504.0)
+        assert float(s) == 2.0 ** round(np.log2(float(s)))
+        hv = h.astype(np.float64)
+        up = np.nextafter(h, np.float16(np.inf)).astype(np.float64)
+        dn = np.nextafter(h, np.float16(-np.inf)).astype(np.float64)
+        err = np.abs(hv - x)
+        assert np.all(err <= np.abs(up - x)) and np.all(err <= np.abs(dn - x))
+
+
+def test_fp16_small_integer_tables_are_exact():
+    """Integers up to 2048 are FP16 values: such a table is stored exactly (s = 1)."""
+    rng = np.random.default_rng(3)
+    lut = rng.integers(-1000, 1048, size=(8, 256)).astype(np.float64)
+    h, s = O.quantize_table_fp16(lut)
+    assert s == 1
+    assert np.array_equal(lut.min(1)[:, None] + h.astype(np.float64), lut)
+
+
+def test_fp16_score_is_distance_within_rounding_bound(small):
+    cb, index = small["cb"], small["index"]
+    lists = index.lists
+    q = small["q"][1]
+    d1, d2 = O.coarse_distances(q, cb)
+    cells, _, _ = O.traverse_full_sort(d1, d2, lists.counts(), 3000)
+    pos = O.candidates(cells, lists)
+    cell = np.repeat(cells, lists.counts()[cells])
+    codes = lists.codes[pos].astype(np.int64)
+    lut = O.pq_table(q, cb)
+    h, s = O.quantize_table_fp16(lut)
+    key32 = (d1[cell // cb.T] + d2[cell % cb.T]).astype(np.float32)
+    cross32 = O.point_cross(cb, index.tables, cell, codes).astype(np.float32)
+    score = (key32 + cross32) + O.shortlist_part(q, cb, codes, "fp16")
+    exact = O.dist_fbpq(q, cb, index.tables, cell, codes)
+    x = lut - lut.min(1)[:, None]
+    tab_err = float(s) * (2.0 ** -11) * x[np.arange(cb.M)[None, :], codes].sum(1)
+    dev = np.abs(score.astype(np.float64) - (exact - lut.min(1).sum()))
+    assert np.all(dev <= tab_err + cb.M * float(s) * 65504.0 * 2.0 ** -23 + 1e-6 * np.abs(exact).max() + 1.0)
+
+
+def test_fp16_full_shortlist_equals_fbpq_search(small):
+    for q in small["q"][:3]:
+        a = O.search_one(small["index"], q, 3000, 50, "fbpq", traversal="full_sort")
+        b = O.search_shortlist_one(small["index"], q, 3000, 50, 10 ** 6, "fp16")
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
