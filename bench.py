@@ -521,7 +521,7 @@ def recall_of(ids, nn):
 
 
 def run_config(args):
-    """The larger configurations: C3 (100M, M = 16: FP32 FBPQ vs the int8 shortlist with
+    """The larger configurations: C3 (100M, M = 16: FP32 FBPQ vs the int8 and FP16 shortlists with
     exact re-scoring at L = 30k), C4 (100M, local codebooks, L = round(10^U(3, 5)) per
     query: HBPQ vs the global codebooks' FBPQ and reconstruction), C5 (1B points:
     batch queries/s per L and Poisson serving latency)."""
@@ -572,18 +572,21 @@ def run_config(args):
         L, S = 30_000, 1000
         ix, out["build_s"] = build("global")
         ms32 = timed(lambda: ix.search(q, L, k, "fbpq"))
-        ms8 = timed(lambda: ix.search_shortlist(q, L, k, shortlist=S))
         a_ids, a_d = ix.search(q, L, k, "fbpq")
-        b_ids, b_d = ix.search_shortlist(q, L, k, shortlist=S)
-        A, B = a_ids.cpu().numpy(), b_ids.cpu().numpy()
-        overlap = np.mean([len(np.intersect1d(A[n], B[n])) / k for n in range(nq)])
+        A = a_ids.cpu().numpy()
         nn = exact_nn_gpu(q[:1000], w, mix, dev)
-        out.update({"L": L, "shortlist": S, "lut": "int8, per-query step, offsets per sub-quantizer",
-                    "fbpq_f32": {"qps": nq / (ms32 / 1e3), "ms": ms32, "recall": recall_of(a_ids[:1000], nn)},
-                    "shortlist_i8": {"qps": nq / (ms8 / 1e3), "ms": ms8, "recall": recall_of(b_ids[:1000], nn)},
-                    "identical_lists": float((a_ids == b_ids).all(1).float().mean()),
-                    "mean_top100_overlap": float(overlap),
-                    "max_abs_dist_diff_same_rank": float((a_d - b_d).abs()[(a_ids == b_ids)].max())})
+        out.update({"L": L, "shortlist": S,
+                    "lut": "int8 (per-query step) and fp16 (power-of-two step), offsets per sub-quantizer",
+                    "fbpq_f32": {"qps": nq / (ms32 / 1e3), "ms": ms32, "recall": recall_of(a_ids[:1000], nn)}})
+        for prec, key in (("int8", "shortlist_i8"), ("fp16", "shortlist_f16")):
+            ms = timed(lambda: ix.search_shortlist(q, L, k, shortlist=S, precision=prec))
+            b_ids, b_d = ix.search_shortlist(q, L, k, shortlist=S, precision=prec)
+            B = b_ids.cpu().numpy()
+            overlap = np.mean([len(np.intersect1d(A[n], B[n])) / k for n in range(nq)])
+            same = a_ids == b_ids
+            out[key] = {"qps": nq / (ms / 1e3), "ms": ms, "recall": recall_of(b_ids[:1000], nn),
+                        "identical_lists": float(same.all(1).float().mean()), "mean_top100_overlap": float(overlap),
+                        "max_abs_dist_diff_same_rank": float((a_d - b_d).abs()[same].max()) if same.any() else None}
     elif args.workload == "c4":
         Ls = np.round(10.0 ** np.random.default_rng(7).uniform(3.0, 5.0, nq)).astype(np.int64)
         out.update({"L": "round(10^U(3,5)) per query, seed 7", "L_mean": float(Ls.mean())})

@@ -223,20 +223,26 @@ int bpq_search(const bpq_index* idx, const float* queries_dev, int64_t nq, const
  * re-scoring (a precision variant of §3.1; the paper scans with full-precision
  * tables).  Per query:
  *  1. the PQ table lut[k][t] of Eq. 8/9 is shifted per sub-quantizer by its
- *     minimum lo_k and quantized with one per-query step s = max_k(max_t lut[k][t]
- *     - lo_k) / 255 (FP32 division; s = 1 if every table is constant):
- *     q8[k][t] = round_half_even((lut[k][t] - lo_k) / s), an integer in [0, 255];
+ *     minimum lo_k; with range = max_k(max_t lut[k][t] - lo_k), in IEEE FP32:
+ *     BPQ_LUT_I8:  step s = range / 255 (s = 1 if range is 0),
+ *                  q8[k][t] = round_half_even((lut[k][t] - lo_k) / s) in [0, 255];
+ *     BPQ_LUT_F16: step s = the smallest power of two >= 1 with range <= 65504 s,
+ *                  h[k][t] = the FP16 value nearest to (lut[k][t] - lo_k) / s
+ *                  (ties to even; the scaling is exact);
  *  2. every candidate of the visited cells (the same cells as bpq_search) gets the
- *     score (key(i,j) + cross(p)) + s * sum_k q8[k][c_k] in FP32, in that order
- *     (the constant sum_k lo_k is left out), and the `shortlist` best by (score,
- *     position in the index lists) are kept;
+ *     score (key(i,j) + cross(p)) + s * part in FP32, in that order, with
+ *     part = sum_k q8[k][c_k] (an exact integer) or the FP32 sum of the h[k][c_k]
+ *     taken in sub-quantizer order k = 0 .. M-1 (the constant sum_k lo_k is left
+ *     out), and the `shortlist` best by (score, position in the index lists) are
+ *     kept;
  *  3. those are re-scored with the exact FBPQ distance (Eq. 8-9, as bpq_search)
  *     and the k best by (distance, id) are returned as by bpq_search.
- *  lut_precision: BPQ_LUT_I8 (the only one); shortlist in [k, 1024].
+ *  lut_precision: BPQ_LUT_I8 or BPQ_LUT_F16; shortlist in [k, 1024].
  *  Needs the global variant.  workspace: bpq_search_shortlist_workspace_size
- *  bytes or fewer (chunks, as bpq_search).  Asynchronous on stream.
+ *  bytes or fewer (chunks, as bpq_search; the same size for both precisions).
+ *  Asynchronous on stream.
  */
-enum { BPQ_LUT_I8 = 1 };
+enum { BPQ_LUT_I8 = 1, BPQ_LUT_F16 = 2 };
 size_t bpq_search_shortlist_workspace_size(const bpq_index* idx, int64_t nq, int64_t L_max, int32_t shortlist);
 int bpq_search_shortlist(const bpq_index* idx, const float* queries_dev, int64_t nq, const int64_t* L_host,
                          int64_t L_stride, int32_t k, int32_t shortlist, int32_t lut_precision, int32_t* ids_dev,

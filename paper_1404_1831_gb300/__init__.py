@@ -19,7 +19,7 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "EIO", -4: "ECORRUPT", -5: "ETIMEOUT",
           -8: "ESTATE"}
 VARIANT_GLOBAL, VARIANT_LOCAL = 0, 1
 SCORERS = {"fbpq": 0, "recon": 1, "hbpq": 2, "fbpq_tables": 3}
-LUT_PRECISIONS = {"int8": 1}
+LUT_PRECISIONS = {"int8": 1, "fp16": 2}
 
 
 class BpqError(RuntimeError):
@@ -308,7 +308,7 @@ class Index:
         return ids, dists
 
     def search_shortlist(self, q, L, k, shortlist=1000, precision="int8", stream=None, workspace=None):
-        """bpq_search_shortlist: int8-table scan to a shortlist, exact FBPQ re-score, top k."""
+        """bpq_search_shortlist: int8- or FP16-table scan to a shortlist, exact FBPQ re-score, top k."""
         import torch
         nq = q.shape[0]
         Ls, stride = _L_array(L, nq)

@@ -264,20 +264,21 @@ void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t*
 }
 
 // ---------------------------------------------------------------------------
-// bpq_search_shortlist: the bpq_search layout plus the int8 tables, their steps
-// and the shortlists.
+// bpq_search_shortlist: the bpq_search layout plus the reduced-precision tables
+// (sized for the 2-byte FP16 form; the int8 form uses the first half), their
+// steps and the shortlists.
 // ---------------------------------------------------------------------------
 struct ShortlistLayout {
   Layout base;
-  size_t lut8, scale, sl, total;
+  size_t lutr, scale, sl, total;
 };
 
 ShortlistLayout shortlist_layout(const bpq_index& ix, int64_t nq, int64_t L_max, int S) {
   ShortlistLayout l{};
   l.base = layout(ix, nq, L_max, BPQ_SCORER_FBPQ, true);
   size_t o = l.base.total;
-  l.lut8 = o;
-  o = align_up(o + (size_t)nq * ix.p.M * KSUB);
+  l.lutr = o;
+  o = align_up(o + (size_t)nq * ix.p.M * KSUB * 2);
   l.scale = o;
   o = align_up(o + (size_t)nq * 4);
   l.sl = o;
@@ -287,13 +288,13 @@ ShortlistLayout shortlist_layout(const bpq_index& ix, int64_t nq, int64_t L_max,
 }
 
 void run_shortlist(const bpq_index& ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride, int k,
-                   int S, int32_t* out_ids, float* out_dists, void* ws, size_t ws_bytes, cudaStream_t st) {
+                   int S, bool f16, int32_t* out_ids, float* out_dists, void* ws, size_t ws_bytes, cudaStream_t st) {
   std::vector<int32_t> Lq;
   const int64_t L_max = read_L(L_host, L_stride, nq, &Lq);
   BPQ_CHECK(k >= 1 && S >= k && S <= MAX_K, BPQ_EINVAL, "need 1 <= k <= shortlist <= 1024");
   check_scorer(ix, BPQ_SCORER_FBPQ);
   BPQ_CHECK(ix.p.D == 128 && (ix.p.M == 8 || ix.p.M == 16), BPQ_EINVAL,
-            "the int8 shortlist is built for D = 128, M = 8 or 16");
+            "the reduced-precision shortlist is built for D = 128, M = 8 or 16");
   if (nq <= 0) return;
   BPQ_CHECK(q && ws && out_ids && out_dists, BPQ_EINVAL, "NULL pointer");
   int64_t chunk = nq;
@@ -316,11 +317,11 @@ void run_shortlist(const bpq_index& ix, const float* q, int64_t nq, const int64_
     float* d1 = reinterpret_cast<float*>(w + l.base.d1);
     float* d2 = reinterpret_cast<float*>(w + l.base.d2);
     float* lut = reinterpret_cast<float*>(w + l.base.lut);
-    uint8_t* lut8 = reinterpret_cast<uint8_t*>(w + l.lut8);
+    void* lutr = w + l.lutr;
     float* scale = reinterpret_cast<float*>(w + l.scale);
     uint64_t* sl = reinterpret_cast<uint64_t*>(w + l.sl);
     launch_query_tables(ix, qc, nc, d1, d2, lut, st);
-    launch_quant_lut(lut, ix.p.M, nc, lut8, scale, st);
+    launch_quant_lut(lut, ix.p.M, nc, lutr, scale, f16, st);
     TraverseArgs ta{};
     ta.d1 = d1;
     ta.d2 = d2;
@@ -344,10 +345,11 @@ void run_shortlist(const bpq_index& ix, const float* q, int64_t nq, const int64_
     launch_traverse(ta, st);
     ScanArgs sa = scan_args(ix, qc, nc, lut, ta.cells, ta.ncells, ta.cap, S, nullptr, nullptr,
                             reinterpret_cast<int32_t*>(w + l.base.qcounter));
-    sa.lut8 = lut8;
+    sa.lut8 = static_cast<const uint8_t*>(lutr);
+    sa.lut16 = static_cast<const uint16_t*>(lutr);
     sa.lut_scale = scale;
     sa.sl_out = sl;
-    launch_scan_q8(sa, st);
+    launch_scan_reduced(sa, f16, st);
     RescoreArgs r{};
     r.sl = sl;
     r.S = S;
@@ -656,9 +658,10 @@ int bpq_search_shortlist(const bpq_index* ix, const float* q, int64_t nq, const 
   return guard([&] {
     check_searchable(ix);
     BPQ_CHECK(nq >= 0, BPQ_EINVAL, "nq < 0");
-    BPQ_CHECK(lut_precision == BPQ_LUT_I8, BPQ_EINVAL, "lut_precision must be BPQ_LUT_I8");
+    BPQ_CHECK(lut_precision == BPQ_LUT_I8 || lut_precision == BPQ_LUT_F16, BPQ_EINVAL,
+              "lut_precision must be BPQ_LUT_I8 or BPQ_LUT_F16");
     DeviceGuard dg(ix->device);
-    run_shortlist(*ix, q, nq, L_host, L_stride, k, shortlist, ids, dists, ws, ws_bytes,
+    run_shortlist(*ix, q, nq, L_host, L_stride, k, shortlist, lut_precision == BPQ_LUT_F16, ids, dists, ws, ws_bytes,
                   static_cast<cudaStream_t>(stream));
   });
 }

@@ -242,15 +242,18 @@ struct ScanArgs {
   float* out_dists;
   int32_t* qcounter;     // work counter for persistent kernels (zeroed by the launcher)
   int sm_count;
-  // int8 shortlist scan (bpq_search_shortlist): per-query int8 table and step,
-  // and the output: the k best (ord(score) << 32 | list position) per query
-  const uint8_t* lut8;   // nq x M x 256
+  // reduced-precision shortlist scan (bpq_search_shortlist): per-query table
+  // (int8, or FP16 bits) and step, and the output: the k best
+  // (ord(score) << 32 | list position) per query
+  const uint8_t* lut8;     // nq x M x 256 (int8 form)
+  const uint16_t* lut16;   // nq x M x 256 (fp16 form)
   const float* lut_scale;  // nq
-  uint64_t* sl_out;      // nq x k
+  uint64_t* sl_out;        // nq x k
 };
 void launch_scan(const ScanArgs& a, int scorer, cudaStream_t st);
-// int8 shortlist scan: sl_out[q][0..k) = the k best (score, position), EMPTY padded.
-void launch_scan_q8(const ScanArgs& a, cudaStream_t st);
+// Shortlist scan with the int8 (f16 = false) or FP16 table: sl_out[q][0..k) =
+// the k best (score, position), EMPTY padded.
+void launch_scan_reduced(const ScanArgs& a, bool f16, cudaStream_t st);
 // Exact FBPQ re-score of the shortlist: per query, the k best (distance, id) of
 // its S shortlisted positions (EMPTY entries skipped).
 struct RescoreArgs {
@@ -268,8 +271,9 @@ struct RescoreArgs {
   float* out_dists;
 };
 void launch_rescore(const RescoreArgs& r, cudaStream_t st);
-// Per-query int8 table and step from the FP32 table (bpq_search_shortlist step 1).
-void launch_quant_lut(const float* lut, int M, int64_t nq, uint8_t* lut8, float* scale, cudaStream_t st);
+// Per-query reduced-precision table and step from the FP32 table (bpq_search_shortlist step 1).
+// out: nq x M x 256 uint8 (int8 form) or FP16 bits (fp16 form).
+void launch_quant_lut(const float* lut, int M, int64_t nq, void* out, float* scale, bool f16, cudaStream_t st);
 bool scan_supported(int D, int M);  // (D, M) shapes the scan kernels are built for
 
 // Index build (bpq_build.cu).

@@ -20,6 +20,8 @@
 // a full buffer is merged by a warp-wide bitonic sort.  A block-wide threshold
 // (the smallest k-th best of any warp) filters candidates; ids are read only for
 // candidates that pass it.  At the end the warp lists are merged by rank.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <type_traits>
 
@@ -294,10 +296,12 @@ __device__ void block_topk_finish(BlockTopK<NT, CAP>& tk, int k, int32_t* out_id
 // FBPQ scan: one CTA per query.
 //  FB_POINT : per-point cross term (one coalesced float per candidate)
 //  FB_TABLES: cross terms gathered from the X1 / X2 tables (2M lookups)
+//  FB_F16   : FP16 table (bpq_search_shortlist): score (key + cross) + s * the FP32
+//             sum, in sub-quantizer order, of M FP16 entries; ranked as FB_Q8
 //  FB_Q8    : int8 table (bpq_search_shortlist): score (key + cross) + s * sum of
 //             M int8 entries, ranked by (score, list position); no id is read
 // ---------------------------------------------------------------------------
-enum { FB_POINT = 0, FB_TABLES = 1, FB_Q8 = 2 };
+enum { FB_POINT = 0, FB_TABLES = 1, FB_Q8 = 2, FB_F16 = 3 };
 
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* dst, const void* src) {
@@ -325,7 +329,7 @@ using CodeVec = typename std::conditional<M == 16, uint4, uint2>::type;
 //  load in flight.
 template <int M, int VAR, int ILP, int CAP, int SUB>
 __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
-  constexpr bool POINT = VAR != FB_TABLES, Q8 = VAR == FB_Q8;
+  constexpr bool POINT = VAR != FB_TABLES, Q8 = VAR == FB_Q8, F16 = VAR == FB_F16, RED = Q8 || F16;
   constexpr int NT = 256, NW = NT / 32, CH = NT, M2 = M / 2;
   constexpr int PER = SUB / NT;      // candidates per thread in the cell map of a slice
   using TK = BlockTopK<NT, CAP>;
@@ -349,12 +353,17 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
   const int k = a.k;
 
   const uint8_t* lut8 = reinterpret_cast<const uint8_t*>(lut);
+  const __half* lut16 = reinterpret_cast<const __half*>(lut);
   for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
     __syncthreads();
     float scale = 0.f;
     if (Q8) {
       const uint4* src = reinterpret_cast<const uint4*>(a.lut8 + q * M * KSUB);
       for (int t = threadIdx.x; t < M * KSUB / 16; t += NT) reinterpret_cast<uint4*>(lut)[t] = src[t];
+      scale = a.lut_scale[q];
+    } else if (F16) {
+      const uint4* src = reinterpret_cast<const uint4*>(a.lut16 + q * M * KSUB);
+      for (int t = threadIdx.x; t < M * KSUB / 8; t += NT) reinterpret_cast<uint4*>(lut)[t] = src[t];
       scale = a.lut_scale[q];
     } else {
       const float4* src = reinterpret_cast<const float4*>(a.lut + q * M * KSUB);
@@ -469,6 +478,11 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
 #pragma unroll
                 for (int kk = 0; kk < M; ++kk) isum += lut8[kk * KSUB + code[u].byte(kk)];
                 part = __fmul_rn(scale, (float)isum);
+              } else if (F16) {
+                float hs = 0.f;  // FP32 additions in sub-quantizer order
+#pragma unroll
+                for (int kk = 0; kk < M; ++kk) hs = __fadd_rn(hs, __half2float(lut16[kk * KSUB + code[u].byte(kk)]));
+                part = __fmul_rn(scale, hs);
               } else if (POINT) {
                 part = pc[u];
 #pragma unroll
@@ -484,10 +498,10 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
                   part += lut[kk * KSUB + b] + xv;
                 }
               }
-              const float dist = Q8 ? __fadd_rn(__fadd_rn(c_key[c], pc[u]), part) : c_key[c] + part;
+              const float dist = RED ? __fadd_rn(__fadd_rn(c_key[c], pc[u]), part) : c_key[c] + part;
               const uint32_t o = f2ord(dist);
               if (o <= th_hi) {
-                comp = ((uint64_t)o << 32) | (Q8 ? pos[u] : (uint32_t)__ldg(a.ids + pos[u]));
+                comp = ((uint64_t)o << 32) | (RED ? pos[u] : (uint32_t)__ldg(a.ids + pos[u]));
                 acc = comp <= th;
               }
             }
@@ -505,7 +519,7 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
         __syncthreads();
       }
     }
-    if (Q8)
+    if (RED)
       block_topk_finish_raw<NT, CAP>(tk, k, a.sl_out + q * k);
     else
       block_topk_finish<NT, CAP>(tk, k, a.out_ids + q * k, a.out_dists + q * k);
@@ -1163,11 +1177,14 @@ bool scan_supported(int D, int M) {
   return (D == 128 && (M == 8 || M == 16)) || (D == 32 && M == 8) || (D == 8 && M == 8);
 }
 
-void launch_scan_q8(const ScanArgs& a, cudaStream_t st) {
+void launch_scan_reduced(const ScanArgs& a, bool f16, cudaStream_t st) {
   if (a.nq <= 0) return;
   BPQ_CHECK(a.k >= 1 && a.k <= MAX_K, BPQ_EINVAL, "shortlist must be in [1, 1024]");
-  BPQ_CHECK(a.D == 128 && (a.M == 8 || a.M == 16), BPQ_EINVAL, "the int8 scan is built for D = 128, M = 8 or 16");
-  if (a.M == 8) run_fbpq<8, FB_Q8>(a, st);
+  BPQ_CHECK(a.D == 128 && (a.M == 8 || a.M == 16), BPQ_EINVAL,
+            "the reduced-precision scan is built for D = 128, M = 8 or 16");
+  if (a.M == 8 && f16) run_fbpq<8, FB_F16>(a, st);
+  else if (a.M == 8) run_fbpq<8, FB_Q8>(a, st);
+  else if (f16) run_fbpq<16, FB_F16>(a, st);
   else run_fbpq<16, FB_Q8>(a, st);
 }
 

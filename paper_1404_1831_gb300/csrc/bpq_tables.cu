@@ -13,6 +13,7 @@
 // For integer-valued inputs (queries in [0, 255], integer codebooks) every
 // product and partial sum here is an integer below 2^24, so FP32 is exact.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -247,12 +248,14 @@ __global__ void cross_table_kernel(const float* __restrict__ C, const float* __r
   X[e] = 2.f * acc;
 }
 
-// bpq_search_shortlist step 1: per query, lo_k = min_t lut[k][t], step
-// s = max_k (max_t lut[k][t] - lo_k) / 255 (1 if that is 0), and
-// q8[k][t] = round_half_even((lut[k][t] - lo_k) / s), all in IEEE FP32.
-template <int M>
+// bpq_search_shortlist step 1: per query, lo_k = min_t lut[k][t] and the
+// widest shifted table range = max_k (max_t lut[k][t] - lo_k), all in IEEE FP32.
+//  int8: step s = range / 255 (1 if range is 0), q8[k][t] = round_half_even((lut[k][t] - lo_k) / s);
+//  fp16: step s = the smallest power of two >= 1 with range <= 65504 s (exact scaling),
+//        h[k][t] = the FP16 value nearest to (lut[k][t] - lo_k) / s (ties to even).
+template <int M, bool F16>
 __global__ void __launch_bounds__(256) quant_lut_kernel(const float* __restrict__ lut, int64_t nq,
-                                                        uint8_t* __restrict__ lut8, float* __restrict__ scale) {
+                                                        void* __restrict__ out, float* __restrict__ scale) {
   __shared__ float lo_s[M];
   __shared__ unsigned int range_bits;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -280,11 +283,21 @@ __global__ void __launch_bounds__(256) quant_lut_kernel(const float* __restrict_
     }
     __syncthreads();
     const float range = __uint_as_float(range_bits);
-    const float s = range > 0.f ? __fdiv_rn(range, 255.f) : 1.f;
+    float s;
+    if (F16) {
+      s = 1.f;
+      while (range > __fmul_rn(65504.f, s)) s = __fmul_rn(s, 2.f);  // range is finite: at most 128 doublings
+    } else {
+      s = range > 0.f ? __fdiv_rn(range, 255.f) : 1.f;
+    }
     for (int e = threadIdx.x; e < M * KSUB; e += 256) {
       const float x = __fsub_rn(L[e], lo_s[e / KSUB]);
-      const int v = __float2int_rn(__fdiv_rn(x, s));
-      lut8[q * M * KSUB + e] = (uint8_t)min(255, max(0, v));
+      if (F16) {
+        static_cast<uint16_t*>(out)[q * M * KSUB + e] = __half_as_ushort(__float2half_rn(__fdiv_rn(x, s)));
+      } else {
+        const int v = __float2int_rn(__fdiv_rn(x, s));
+        static_cast<uint8_t*>(out)[q * M * KSUB + e] = (uint8_t)min(255, max(0, v));
+      }
     }
     if (threadIdx.x == 0) scale[q] = s;
   }
@@ -292,12 +305,14 @@ __global__ void __launch_bounds__(256) quant_lut_kernel(const float* __restrict_
 
 }  // namespace
 
-void launch_quant_lut(const float* lut, int M, int64_t nq, uint8_t* lut8, float* scale, cudaStream_t st) {
+void launch_quant_lut(const float* lut, int M, int64_t nq, void* out, float* scale, bool f16, cudaStream_t st) {
   if (nq <= 0) return;
   const int grid = (int)std::min<int64_t>(nq, 1 << 20);
-  if (M == 8) quant_lut_kernel<8><<<grid, 256, 0, st>>>(lut, nq, lut8, scale);
-  else if (M == 16) quant_lut_kernel<16><<<grid, 256, 0, st>>>(lut, nq, lut8, scale);
-  else throw Error(BPQ_EINVAL, "the int8 table is built for M = 8 or 16");
+  if (M == 8 && f16) quant_lut_kernel<8, true><<<grid, 256, 0, st>>>(lut, nq, out, scale);
+  else if (M == 8) quant_lut_kernel<8, false><<<grid, 256, 0, st>>>(lut, nq, out, scale);
+  else if (M == 16 && f16) quant_lut_kernel<16, true><<<grid, 256, 0, st>>>(lut, nq, out, scale);
+  else if (M == 16) quant_lut_kernel<16, false><<<grid, 256, 0, st>>>(lut, nq, out, scale);
+  else throw Error(BPQ_EINVAL, "the reduced-precision table is built for M = 8 or 16");
   check_launch("table quantization kernel");
 }
 

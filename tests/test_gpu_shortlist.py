@@ -1,5 +1,6 @@
-"""GPU parity of the int8-table shortlist search (bpq_search_shortlist) and of the
-M = 16 scans against the FP64 oracle, on the tiny workload (100k points, T = 64)."""
+"""GPU parity of the reduced-precision shortlist search (bpq_search_shortlist, int8 and
+FP16 tables) and of the M = 16 scans against the oracle, on the tiny workload (100k
+points, T = 64)."""
 import numpy as np
 import pytest
 
@@ -37,19 +38,20 @@ def m16(tiny_oracle):
                 q=torch.as_tensor(t["queries"][:40], dtype=torch.float32, device=DEV))
 
 
-def _check(fx, L, k, S, nq=None):
+def _check(fx, L, k, S, nq=None, precision="int8"):
     nq = nq or len(fx["qh"])
-    ids, dists = fx["ix"].search_shortlist(fx["q"][:nq], L, k, shortlist=S)
-    o_ids, o_d = O.search_shortlist(fx["index"], fx["qh"][:nq], L, k, S)
+    ids, dists = fx["ix"].search_shortlist(fx["q"][:nq], L, k, shortlist=S, precision=precision)
+    o_ids, o_d = O.search_shortlist(fx["index"], fx["qh"][:nq], L, k, S, precision)
     ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
     assert np.array_equal(ids, o_ids), "shortlist ids differ"
     assert np.array_equal(dists.astype(np.float64), o_d), "shortlist distances differ"
     return ids, dists
 
 
+@pytest.mark.parametrize("precision", ["int8", "fp16"])
 @pytest.mark.parametrize("L,k,S", [(10_000, 100, 1000), (3_000, 10, 100), (10_000, 100, 100), (20_000, 1, 1024)])
-def test_shortlist_matches_oracle_m8(m8, L, k, S):
-    _check(m8, L, k, S, nq=40)
+def test_shortlist_matches_oracle_m8(m8, L, k, S, precision):
+    _check(m8, L, k, S, nq=40, precision=precision)
 
 
 def test_shortlist_pads_when_few_candidates(m8):
@@ -73,8 +75,15 @@ def test_fbpq_and_reconstruction_match_oracle_m16(m16):
         assert exact == len(o_ids)
 
 
-def test_shortlist_matches_oracle_m16(m16):
-    _check(m16, 10_000, 100, 1000)
+@pytest.mark.parametrize("precision", ["int8", "fp16"])
+def test_shortlist_matches_oracle_m16(m16, precision):
+    _check(m16, 10_000, 100, 1000, precision=precision)
+
+
+def test_fp16_short_shortlist_ranks_like_the_oracle(m8):
+    """A shortlist much shorter than the candidate list (S = k = 10) depends on the
+    FP16 scores themselves, not only on the exact re-score."""
+    _check(m8, 10_000, 10, 10, nq=40, precision="fp16")
 
 
 def test_shortlist_rejects_bad_arguments(m8):
