@@ -13,7 +13,7 @@ Product Quantization for Billion-Scale Approximate Nearest Neighbors in High
 Dimensions" (arXiv:1404.1831) that its docstring names.  Arithmetic is FP64 for
 distances and exact integer (int64 / Python int) for k-means means.
 
-Readings of points the paper leaves open (each is also listed in the design doc):
+Readings of points the paper leaves open:
   * Codebooks live on the integer grid: every k-means update rounds the mean
     half up to an integer, floor((2*sum + n) / (2*n)).  Points are integers in
     [0, 255], so every distance in this module is an exact integer below 2^53 and
