@@ -179,7 +179,7 @@ def test_fbpq_equals_reconstruction_on_gpu(gpu):
         assert np.array_equal(a[0], b[0]) and close(a[1], b[1]).all()
 
 
-@pytest.mark.parametrize("k", [1, 7, 128, 300, 1024])
+@pytest.mark.parametrize("k", [1, 7, 128, 129, 300, 1024])
 def test_search_k_values(gpu, tiny_oracle, k):
     L = 3000
     ids, dists = gpu["ix"].search(gpu["q"][:12], L, k, "fbpq")
@@ -293,3 +293,26 @@ def test_serving_answers_equal_batch_search(gpu, tiny_oracle):
     assert (res.latency_s > 0).all()
     s = res.summary()
     assert s["p50_ms"] <= s["p99_ms"] <= s["max_ms"]
+
+
+@pytest.mark.parametrize("k", [10, 100, 128])
+def test_search_with_large_tie_groups(tiny_oracle, k):
+    """40 points, each added 500 times under distinct ids: every distance is shared by
+    500 candidates, so the scan's buffers fill with entries tied at their cut value
+    (the exact re-rank by (distance, id)) and the final survivors exceed 128 (the rank
+    count); the lists equal the oracle's, ties by id."""
+    import paper_1404_1831_gb300 as bpq
+    t = tiny_oracle
+    cb = t["cb"]
+    base = np.repeat(t["base"][:40], 500, axis=0)
+    index = O.build_index(cb, base)
+    ix = bpq.Index.create(cb.C1, cb.C2, cb.R)
+    ix.add(torch.as_tensor(base, dtype=torch.float32, device=DEV))
+    ix.finalize()
+    q = t["queries"][:8]
+    ids, dists = ix.search(torch.as_tensor(q, dtype=torch.float32, device=DEV), len(base), k, "fbpq")
+    o_ids, o_d, _ = O.search(index, q, len(base), k, "fbpq")
+    ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+    assert np.array_equal(ids, o_ids)
+    assert np.array_equal(dists.astype(np.float64), o_d)
+    ix.close()
