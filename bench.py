@@ -217,7 +217,13 @@ class ClockSampler:
 
 
 def source_digest(path):
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    """Digest of a source file's code: comments, blank lines and trailing blanks are left out, so a
+    comment edit keeps the recorded counters of an unchanged kernel."""
+    import re
+    text = open(path, encoding="utf-8").read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln).encode()).hexdigest()[:16]
 
 
 def recorded_traffic(kernel_file):

@@ -540,10 +540,12 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
 //
 // Top-k: a candidate whose distance passes the block threshold goes to its
 // warp's buffer as (ord(distance) << 32 | list position).  A full buffer is cut
-// by a warp radix select to the entries with distance <= its k-th smallest
-// distance v, and the block threshold drops to min(threshold, v): every warp's
-// v bounds the k-th best distance of the whole query, and ties at v stay
-// accepted.  Ids are read only at the end, for the survivors, which are ranked
+// to the entries with distance <= v, a value with at least k entries at or
+// below it (a count bisection, stopped once k .. k + 32 remain), and the block
+// threshold drops to min(threshold, v): at least k candidates of the query lie
+// at or below every warp's v, so no candidate above it can rank, and ties at v
+// stay accepted.  At the end the entries within the threshold are gathered, cut
+// the same way over the block, given their ids (the only id reads) and ranked
 // exactly by (distance, id).
 // ---------------------------------------------------------------------------
 constexpr uint32_t NO_POS = 0xffffffffu;
