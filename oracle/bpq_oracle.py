@@ -28,10 +28,13 @@ Readings of points the paper leaves open:
     and distance +inf.  The true nearest neighbour breaks ties by lowest id.
 
 Parity pins (tests/test_oracle_*.py) tie each function to something other than
-itself: brute force on tiny inputs, hand-checkable k-means cases, the
-multi-sequence heap against the full-sort definition, the FBPQ decomposition
-against explicit reconstruction, the zero-quantization special case against
-brute-force k-NN, and the paper's printed memory sizes.
+itself: brute force on tiny inputs, hand-checkable k-means cases, codebook
+training on learn sets whose coarse centroids and residual codebooks are written
+out by hand (global and local), the multi-sequence heap against the full-sort
+definition, hand-computed reconstructions (Eq. 7 and §3.2), the FBPQ
+decomposition and the HBPQ table regrouping against explicit reconstruction, the
+zero-quantization special case against brute-force k-NN, and the paper's printed
+memory sizes.
 """
 
 from __future__ import annotations
@@ -345,6 +348,49 @@ def reconstruct_hbpq(cb: Codebooks, cell, codes):
     return np.concatenate([cb.C1[i] + r1, cb.C2[j] + r2], axis=1).astype(np.float64)
 
 
+def hbpq_tables(q, cb: Codebooks, i, j):
+    """Per-query lookup tables of HBPQ for the half-cells i (first half) and j
+    (second half): the O(D) reconstruction distance of §3.2 regrouped so that a
+    point costs M lookups.  With r^1 = [Q^i_1[c_1] .. Q^i_{M/2}[c_{M/2}]],
+        ||q^1 - c^1_i - r^1||^2 = ||q^1 - c^1_i||^2
+                                  + sum_k ( ||Q^i_k[c_k]||^2 - 2 <q_k - c^1_i|k, Q^i_k[c_k]> )
+    (c^1_i|k: block k of c^1_i), and likewise for the second half with S^j and c^2_j.
+    Returns A (M/2, 256) and B (M/2, 256), FP64:
+        A[k][t] = ||Q^i_k[t]||^2 + 2 <c^1_i|k, Q^i_k[t]> - 2 <q_k, Q^i_k[t]>
+        B[k][t] = ||S^j_k[t]||^2 + 2 <c^2_j|k, S^j_k[t]> - 2 <q_{M/2+k}, S^j_k[t]>
+    so that ||q - xhat||^2 = d1[i] + d2[j] + sum_k A[k][c_k] + sum_k B[k][c_{M/2+k}]."""
+    q = np.asarray(q, np.float64)
+    s, m2, h = cb.sub, cb.M // 2, cb.D // 2
+    A = np.empty((m2, KSUB))
+    B = np.empty((m2, KSUB))
+    for k in range(m2):
+        Qk = cb.Q[i, k].astype(np.float64)
+        Sk = cb.S[j, k].astype(np.float64)
+        c1 = cb.C1[i, k * s:(k + 1) * s].astype(np.float64)
+        c2 = cb.C2[j, k * s:(k + 1) * s].astype(np.float64)
+        A[k] = (Qk * Qk).sum(1) + 2.0 * (Qk @ c1) - 2.0 * (Qk @ q[k * s:(k + 1) * s])
+        B[k] = (Sk * Sk).sum(1) + 2.0 * (Sk @ c2) - 2.0 * (Sk @ q[h + k * s:h + (k + 1) * s])
+    return A, B
+
+
+def dist_hbpq_tables(q, cb: Codebooks, cell, codes):
+    """HBPQ distance of every point through hbpq_tables: d1[i] + d2[j] plus M
+    lookups, one table pair per distinct half-cell pair (i, j)."""
+    cell = np.asarray(cell, dtype=np.int64)
+    codes = np.asarray(codes, dtype=np.int64)
+    m2 = cb.M // 2
+    d1, d2 = coarse_distances(q, cb)
+    i, j = cell // cb.T, cell % cb.T
+    out = np.empty(len(cell))
+    for ii, jj in sorted(set(zip(i.tolist(), j.tolist()))):
+        sel = (i == ii) & (j == jj)
+        A, B = hbpq_tables(q, cb, ii, jj)
+        c = codes[sel]
+        out[sel] = (d1[ii] + d2[jj] + sum(A[k][c[:, k]] for k in range(m2))
+                    + sum(B[k][c[:, m2 + k]] for k in range(m2)))
+    return out
+
+
 def dist_reconstruct(q, xhat):
     """Multi-D-ADC distance (§2.3.3): ||q - xhat||^2 from the explicit reconstruction, O(D) per point."""
     diff = np.asarray(q, np.float64)[None, :] - xhat
@@ -528,7 +574,7 @@ def topk(dists, ids, k):
     return out_i, out_d
 
 
-SCORERS = ("fbpq", "recon", "hbpq")
+SCORERS = ("fbpq", "recon", "hbpq", "hbpq_tables")
 
 
 @dataclasses.dataclass
@@ -580,6 +626,10 @@ def search_one(index: OracleIndex, q, L, k, scorer="fbpq", traversal="multiseque
         if index.variant != "local":
             raise ValueError("hbpq scores local codes")
         dist = dist_reconstruct(q, reconstruct_hbpq(cb, cell_of, codes))
+    elif scorer == "hbpq_tables":
+        if index.variant != "local":
+            raise ValueError("hbpq scores local codes")
+        dist = dist_hbpq_tables(q, cb, cell_of, codes)
     else:
         raise ValueError(scorer)
     ids, dd = topk(dist, lists.ids[pos], k)

@@ -64,14 +64,31 @@ def test_build_lists_layout():
     assert L.counts().sum() == 6
 
 
-def test_reconstruct_is_equation_7():
-    rng = np.random.default_rng(12)
-    cb = small_codebooks(rng)
-    cell = np.array([1 * 4 + 3])
-    code = np.array([[5, 6, 7, 8]])
-    xh = O.reconstruct(cb, cell, code)[0]
-    expect = np.concatenate([cb.C1[1], cb.C2[3]]) + np.concatenate([cb.R[k][code[0, k]] for k in range(4)])
-    assert np.array_equal(xh, expect)
+def literal_codebooks():
+    """D = 4, T = 2, M = 2 codebooks with entries chosen by hand:
+    C^1 = [[1, 2], [3, 4]], C^2 = [[5, 6], [7, 8]], R_0[t] = (t, -t), R_1[t] = (2t, 1);
+    local codebooks Q^i_0[t] = (10 i + t, 0), S^j_0[t] = (0, -t - j)."""
+    t = np.arange(O.KSUB)
+    R = np.stack([np.stack([t, -t], 1), np.stack([2 * t, np.ones_like(t)], 1)])
+    Q = np.stack([np.stack([10 * i + t, 0 * t], 1)[None] for i in range(2)])
+    S = np.stack([np.stack([0 * t, -t - j], 1)[None] for j in range(2)])
+    return O.Codebooks(D=4, T=2, M=2, C1=np.array([[1, 2], [3, 4]]), C2=np.array([[5, 6], [7, 8]]), R=R, Q=Q, S=S)
+
+
+def test_reconstruct_literal_equation_7():
+    """Eq. 7 by hand: cell (i, j) = (1, 0), code (3, 5):
+    [c^1_1; c^2_0] + [R_0[3]; R_1[5]] = [3, 4, 5, 6] + [3, -3, 10, 1] = [6, 1, 15, 7]."""
+    cb = literal_codebooks()
+    xh = O.reconstruct(cb, np.array([1 * 2 + 0]), np.array([[3, 5]]))
+    assert xh.tolist() == [[6.0, 1.0, 15.0, 7.0]]
+
+
+def test_reconstruct_hbpq_literal():
+    """HBPQ reconstruction (§3.2) by hand: cell (1, 1), code (3, 5) uses Q^1_0 and
+    S^1_0: [3, 4] + (13, 0) and [7, 8] + (0, -6) -> [16, 4, 7, 2]."""
+    cb = literal_codebooks()
+    xh = O.reconstruct_hbpq(cb, np.array([1 * 2 + 1]), np.array([[3, 5]]))
+    assert xh.tolist() == [[16.0, 4.0, 7.0, 2.0]]
 
 
 def test_train_shapes_and_local_training_improves_distortion():

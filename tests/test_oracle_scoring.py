@@ -125,3 +125,69 @@ def test_memory_formulas_reproduce_paper():
     e = g["hbpq_gist50m_local"]
     extra = O.hbpq_local_floats(e["T"], e["D"], e["K"]) * 4 / 2 ** 30
     assert abs(extra - (e["printed_after_gb"] - e["printed_before_gb"])) < 0.01
+
+
+def test_hbpq_tables_literal():
+    """The regrouped HBPQ distance by hand (literal codebooks of the encode pins:
+    C^1 = [[1, 2], [3, 4]], C^2 = [[5, 6], [7, 8]], Q^i_0[t] = (10 i + t, 0),
+    S^j_0[t] = (0, -t - j)).  Query q = (10, 0, 5, 5), cell (1, 1), code (3, 5):
+      xhat = [3 + 13, 4 + 0, 7 + 0, 8 - 6] = [16, 4, 7, 2], ||q - xhat||^2 = 36 + 16 + 4 + 9 = 65;
+      d1[1] = 7^2 + 4^2 = 65, d2[1] = 2^2 + 3^2 = 13;
+      A[0][3] = 13^2 + 2 (3*13 + 4*0) - 2 (10*13 + 0*0) = 169 + 78 - 260 = -13;
+      B[0][5] = 6^2 + 2 (7*0 + 8*(-6)) - 2 (5*0 + 5*(-6)) = 36 - 96 + 60 = 0;
+      65 + 13 - 13 + 0 = 65."""
+    from test_oracle_encode import literal_codebooks
+    cb = literal_codebooks()
+    q = np.array([10, 0, 5, 5])
+    A, B = O.hbpq_tables(q, cb, 1, 1)
+    assert A[0][3] == -13.0 and B[0][5] == 0.0
+    assert O.dist_hbpq_tables(q, cb, np.array([3]), np.array([[3, 5]])).tolist() == [65.0]
+
+
+@pytest.fixture(scope="module")
+def tiny_local(tiny_oracle):
+    cb = O.train_hbpq_local(tiny_oracle["learn"], tiny_oracle["cb"], 3)
+    X = tiny_oracle["base"][:20000]
+    return cb, O.build_index(cb, X, variant="local")
+
+
+def test_hbpq_tables_equal_reconstruction_bit_exact(tiny_oracle, tiny_local):
+    """The table form is an exact regrouping of the O(D) HBPQ reconstruction
+    distance (§3.2): equal bit for bit on the integer grid, and the searches agree."""
+    cb, idx = tiny_local
+    lists = idx.lists
+    rng = np.random.default_rng(5)
+    pos = rng.integers(0, len(lists.ids), size=3000)
+    cell_of = np.searchsorted(lists.offsets, pos, side="right") - 1
+    for q in tiny_oracle["queries"][:6]:
+        a = O.dist_hbpq_tables(q, cb, cell_of, lists.codes[pos])
+        b = O.dist_reconstruct(q, O.reconstruct_hbpq(cb, cell_of, lists.codes[pos]))
+        assert np.array_equal(a, b)
+    Q = tiny_oracle["queries"][:8]
+    ra = O.search(idx, Q, 3000, 50, "hbpq_tables")
+    rb = O.search(idx, Q, 3000, 50, "hbpq")
+    assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1])
+
+
+def test_hbpq_tables_catch_dropped_or_swapped_terms(tiny_oracle, tiny_local):
+    """Plausible mistakes in the table form differ from the reconstruction: the
+    cross term 2<c^1_i|k, Q^i_k[t]> left out, or the global R_k used in place of
+    the local codebooks."""
+    cb, idx = tiny_local
+    q = tiny_oracle["queries"][0]
+    lists = idx.lists
+    pos = np.arange(0, len(lists.ids), 13)
+    cell_of = np.searchsorted(lists.offsets, pos, side="right") - 1
+    truth = O.dist_reconstruct(q, O.reconstruct_hbpq(cb, cell_of, lists.codes[pos]))
+    no_cross = O.Codebooks(D=cb.D, T=cb.T, M=cb.M, C1=np.zeros_like(cb.C1), C2=cb.C2, R=cb.R, Q=cb.Q, S=cb.S)
+    i = cell_of // cb.T
+    d1_true, _ = O.coarse_distances(q, cb)
+    d1_zero, _ = O.coarse_distances(q, no_cross)
+    # the same tables with c^1 zeroed in the cross term only: add back the true d1
+    wrong = O.dist_hbpq_tables(q, no_cross, cell_of, lists.codes[pos]) - d1_zero[i] + d1_true[i]
+    assert not np.array_equal(wrong, truth)
+    m2 = cb.M // 2
+    glob = O.Codebooks(D=cb.D, T=cb.T, M=cb.M, C1=cb.C1, C2=cb.C2, R=cb.R,
+                       Q=np.broadcast_to(cb.R[:m2], cb.Q.shape).copy(),
+                       S=np.broadcast_to(cb.R[m2:], cb.S.shape).copy())
+    assert not np.array_equal(O.dist_hbpq_tables(q, glob, cell_of, lists.codes[pos]), truth)
