@@ -61,9 +61,19 @@ enum {
                            costs M table lookups plus one stored scalar */
   BPQ_SCORER_RECON = 1, /* Multi-D-ADC: per-cell query displacement and explicit
                            reconstruction, O(D) per candidate (§2.3.3) */
-  BPQ_SCORER_HBPQ = 2,  /* HBPQ: reconstruction with local codebooks, O(D) (§3.2) */
-  BPQ_SCORER_FBPQ_TABLES = 3 /* Eq. 8 with Eq. 9 evaluated from the T*M*K cross tables of
+  BPQ_SCORER_HBPQ = 2,  /* HBPQ distance (§3.2: reconstruction with the local codebooks
+                           Q^i_k, S^j_k of the cell's half-cells), evaluated through
+                           per-(query, visited half-cell) tables built on the tensor
+                           cores: A_i[k][t] = ||Q^i_k[t]||^2 + 2<c^1_i|k, Q^i_k[t]>
+                           - 2<q_k, Q^i_k[t]> (B_j likewise), so a candidate costs M
+                           lookups: d1[i] + d2[j] + sum_k A_i[k][c_k] + sum_k B_j[k][c_{M/2+k}].
+                           An exact regrouping of the O(D) distance.  For k > 128, and
+                           for queries whose tables do not fit the workspace, the O(D)
+                           form below is used. */
+  BPQ_SCORER_FBPQ_TABLES = 3, /* Eq. 8 with Eq. 9 evaluated from the T*M*K cross tables of
                            §3.3 at query time: 2M table lookups per candidate */
+  BPQ_SCORER_HBPQ_RECON = 4 /* HBPQ as the paper evaluates it (§3.2): explicit
+                           reconstruction with the local codebooks, O(D) per candidate */
 };
 
 typedef struct bpq_index bpq_index;
@@ -206,7 +216,8 @@ int bpq_traverse(const bpq_index* idx, const float* queries_dev, int64_t nq, con
  * ||q - x^||^2 (Eq. 8), ascending, ties by id; slots beyond the candidate count
  * hold id -1 and distance +inf.
  *  queries_dev: nq x D float32; k in [1, 1024]; scorer: BPQ_SCORER_*
- *  (FBPQ, FBPQ_TABLES and RECON need the global variant, HBPQ the local one).
+ *  (FBPQ, FBPQ_TABLES and RECON need the global variant, HBPQ and HBPQ_RECON the
+ *  local one).
  *  ids_dev: nq x k int32; dists_dev: nq x k float32.
  *  workspace_dev: at least bpq_search_workspace_size(idx, nq, max L, k, scorer)
  *  bytes, or fewer: queries are then processed in chunks that fit (at least one
@@ -262,9 +273,11 @@ int bpq_scan(const bpq_index* idx, const float* queries_dev, int64_t nq, const f
              int32_t* ids_dev, float* dists_dev, int32_t* counter_dev, void* stream);
 
 /*
- * bpq_search_status — synchronizes the stream and returns BPQ_OK, or
- * BPQ_ECAPACITY if any query of the last bpq_search / bpq_traverse on this
- * workspace overflowed a fixed-size buffer.
+ * bpq_search_status — synchronizes the stream and returns BPQ_OK; BPQ_ETIMEOUT if
+ * a bounded device wait of the last bpq_search / bpq_traverse on this workspace
+ * gave up (a tensor-core table tile whose MMA did not signal completion; that tile
+ * was recomputed on the CUDA cores, so the results are still complete); or
+ * BPQ_ECAPACITY if a query overflowed a fixed-size buffer.
  */
 int bpq_search_status(const bpq_index* idx, void* workspace_dev, void* stream);
 
@@ -304,6 +317,19 @@ int bpq_search_host(bpq_index* idx, const float* queries_host, int64_t nq, const
 int bpq_search_noalloc(const bpq_index* idx, const float* queries_dev, int64_t nq, const int64_t* L_host,
                        int64_t L_stride, int32_t k, int32_t scorer, int32_t* ids_dev, float* dists_dev,
                        int32_t* status_dev, void* stream);
+
+/*
+ * bpq_set_hbpq_table_budget — table slots reserved per query for the HBPQ table
+ * form of bpq_search (BPQ_SCORER_HBPQ).  One slot is one (query, visited
+ * half-cell) table of M/2 x 256 floats (4 KB at M = 8); a query visits one slot
+ * per distinct row i and per distinct column j of its visited cells.  0 (the
+ * default) reserves about 4 sqrt(L / rho) + 32 slots per query (rho = points per
+ * non-empty cell, at most 2T).  A query whose slots do not fit the reserved area is
+ * scored with the O(D) reconstruction instead, with the same results.  The value
+ * also sizes bpq_search_workspace_size.  Errors: BPQ_EINVAL (NULL index, negative
+ * or non-finite value).
+ */
+int bpq_set_hbpq_table_budget(bpq_index* idx, double slots_per_query);
 
 /* bpq_info / bpq_arrays — sizes and read-only device views (see the structs). */
 int bpq_get_info(const bpq_index* idx, bpq_info* out);

@@ -18,7 +18,7 @@ BPQ_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "EIO", -4: "ECORRUPT", -5: "ETIMEOUT", -6: "ECUDA", -7: "ECAPACITY",
           -8: "ESTATE"}
 VARIANT_GLOBAL, VARIANT_LOCAL = 0, 1
-SCORERS = {"fbpq": 0, "recon": 1, "hbpq": 2, "fbpq_tables": 3}
+SCORERS = {"fbpq": 0, "recon": 1, "hbpq": 2, "fbpq_tables": 3, "hbpq_recon": 4}
 LUT_PRECISIONS = {"int8": 1, "fp16": 2}
 
 
@@ -63,6 +63,7 @@ _SIGS = {
     "bpq_search": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P,
                                   _P, _P, ctypes.c_size_t, _P]),
     "bpq_search_status": (ctypes.c_int, [_P, _P, _P]),
+    "bpq_set_hbpq_table_budget": (ctypes.c_int, [_P, ctypes.c_double]),
     "bpq_search_shortlist_workspace_size": (ctypes.c_size_t, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32]),
     "bpq_search_shortlist": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_size_t, _P]),
@@ -339,6 +340,10 @@ class Index:
         if rc != BPQ_OK:
             raise BpqError(rc, "bpq_search_noalloc failed")
         return ids, dists
+
+    def set_hbpq_table_budget(self, slots_per_query):
+        """Table slots reserved per query by the HBPQ table form (0 = automatic)."""
+        _check(lib().bpq_set_hbpq_table_budget(self._h, float(slots_per_query)))
 
     def search_status(self, workspace=None, stream=None):
         ws = workspace if workspace is not None else self._ws

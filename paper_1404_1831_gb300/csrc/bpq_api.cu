@@ -2,6 +2,7 @@
 // workspace layout and the query pipeline
 //   tables (K1/K2) -> traversal (K4) -> scan + top-k (K5/K6)
 // enqueued on the caller's stream, chunk by chunk when the workspace is small.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -92,14 +93,33 @@ size_t cb_floats_local(const bpq_params& p) { return (size_t)p.T * (p.M / 2) * K
 // ---------------------------------------------------------------------------
 bool uses_lut(int scorer);
 
+// The HBPQ table form (BPQ_SCORER_HBPQ, k <= 128) adds per query its table slots
+// and bitmaps, per half-cell the bitmap of visiting queries, and the tables.
+bool hbpq_tables_used(int scorer, int k) { return scorer == BPQ_SCORER_HBPQ && k <= 128; }
+
+// Table slots expected for a query at budget L: about 4 sqrt(L / rho) + 32 distinct
+// rows and columns (the visited cells of a query fill a region of the key grid a
+// few times wider than sqrt(#cells) in each direction; rho = points per non-empty
+// cell), at most 2T.  A query whose slots do not fit is scored by the O(D) form.
+double hbpq_slots_per_query(const bpq_index& ix, double L) {
+  if (ix.hb_slots_per_query > 0.0) return ix.hb_slots_per_query;
+  const double rho = std::max(1.0, (double)ix.n_points / (double)std::max<int64_t>(1, ix.n_nonempty));
+  return std::min(2.0 * ix.p.T, 4.0 * std::ceil(std::sqrt(std::max(1.0, L / rho))) + 32.0);
+}
+
+// Table offsets are 32-bit float indices in the scan.
+int64_t hbpq_slot_limit(const bpq_index& ix) { return (((int64_t)1 << 32) - 1) / ((int64_t)ix.m2 * KSUB); }
+
 struct Layout {
   size_t status, qcounter, L, d1, d2, lut, cells, ncells, npoints, total;
-  int64_t cap;
+  size_t hb_qbase, hb_qrows, hb_qbits, hb_hmap, hb_ctr, hb_fb, hb_tab;
+  int64_t cap, hb_slots;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-Layout layout(const bpq_index& ix, int64_t nq, int64_t L_max, int scorer, bool with_cells) {
+Layout layout(const bpq_index& ix, int64_t nq, int64_t L_max, int scorer, bool with_cells, int k = 1,
+              double hb_per_query = 0.0) {
   Layout l{};
   size_t o = 0;
   l.status = o;
@@ -121,6 +141,25 @@ Layout layout(const bpq_index& ix, int64_t nq, int64_t L_max, int scorer, bool w
   o = align_up(o + (size_t)nq * 4);
   l.npoints = o;
   o = align_up(o + (size_t)nq * 8);
+  if (with_cells && hbpq_tables_used(scorer, k)) {
+    const int TW = (ix.p.T + 31) / 32;
+    if (hb_per_query <= 0.0) hb_per_query = hbpq_slots_per_query(ix, (double)L_max);
+    l.hb_slots = std::min<int64_t>(hbpq_slot_limit(ix), (int64_t)std::ceil(hb_per_query * (double)nq));
+    l.hb_qbase = o;
+    o = align_up(o + (size_t)nq * 4);
+    l.hb_qrows = o;
+    o = align_up(o + (size_t)nq * 4);
+    l.hb_qbits = o;
+    o = align_up(o + (size_t)nq * 2 * TW * 4);
+    l.hb_hmap = o;
+    o = align_up(o + (size_t)2 * ix.p.T * ((nq + 31) / 32) * 4);
+    l.hb_ctr = o;
+    o = align_up(o + 16);
+    l.hb_fb = o;
+    o = align_up(o + (size_t)nq * 4);
+    l.hb_tab = o;
+    o = align_up(o + (size_t)l.hb_slots * ix.m2 * KSUB * 4);
+  }
   l.total = o;
   return l;
 }
@@ -178,8 +217,8 @@ ScanArgs scan_args(const bpq_index& ix, const float* q, int64_t nq, const float*
 bool uses_lut(int scorer) { return scorer == BPQ_SCORER_FBPQ || scorer == BPQ_SCORER_FBPQ_TABLES; }
 
 void check_scorer(const bpq_index& ix, int scorer) {
-  BPQ_CHECK(scorer >= BPQ_SCORER_FBPQ && scorer <= BPQ_SCORER_FBPQ_TABLES, BPQ_EINVAL, "bad scorer");
-  if (scorer == BPQ_SCORER_HBPQ)
+  BPQ_CHECK(scorer >= BPQ_SCORER_FBPQ && scorer <= BPQ_SCORER_HBPQ_RECON, BPQ_EINVAL, "bad scorer");
+  if (scorer == BPQ_SCORER_HBPQ || scorer == BPQ_SCORER_HBPQ_RECON)
     BPQ_CHECK(ix.p.variant == BPQ_VARIANT_LOCAL, BPQ_EINVAL, "the HBPQ scorer needs local codebooks");
   else
     BPQ_CHECK(ix.p.variant == BPQ_VARIANT_GLOBAL, BPQ_EINVAL, "FBPQ and reconstruction scorers need global codebooks");
@@ -206,18 +245,33 @@ void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t*
     BPQ_CHECK(out_ids && out_dists, BPQ_EINVAL, "output pointers are NULL");
   else
     BPQ_CHECK(user_ncells && user_npoints, BPQ_EINVAL, "bad traversal outputs");
-  // largest chunk that fits
+  const bool hb = scan && hbpq_tables_used(scorer, k);
+  // HBPQ table slots per query: the mean of the per-query expectation
+  double hb_per_query = 0.0;
+  if (hb) {
+    if (L_stride) {
+      for (int32_t v : Lq) hb_per_query += hbpq_slots_per_query(ix, (double)v);
+      hb_per_query /= (double)nq;
+    } else {
+      hb_per_query = hbpq_slots_per_query(ix, (double)L_max);
+    }
+  }
+  auto lay = [&](int64_t n) { return layout(ix, n, L_max, scorer, scan, k, hb_per_query); };
+  // largest chunk that fits the workspace (and, for HBPQ, whose table offsets fit 32 bits)
+  auto fits = [&](int64_t n) {
+    return lay(n).total <= ws_bytes && !(hb && hb_per_query * (double)n > (double)hbpq_slot_limit(ix));
+  };
   int64_t chunk = nq;
-  if (layout(ix, chunk, L_max, scorer, scan).total > ws_bytes) {
+  if (!fits(chunk)) {
     int64_t lo = 0, hi = nq;
     while (hi - lo > 1) {
-      int64_t mid = (lo + hi) / 2;
-      if (layout(ix, mid, L_max, scorer, scan).total <= ws_bytes) lo = mid; else hi = mid;
+      const int64_t mid = (lo + hi) / 2;
+      if (fits(mid)) lo = mid; else hi = mid;
     }
     chunk = lo;
   }
   BPQ_CHECK(chunk >= 1, BPQ_ECAPACITY, "workspace too small for one query");
-  const Layout l = layout(ix, chunk, L_max, scorer, scan);
+  const Layout l = lay(chunk);
   char* w = static_cast<char*>(ws);
   BPQ_CUDA(cudaMemsetAsync(w + l.status, 0, 4, st));
   const float rho = (float)((double)ix.n_points / (double)std::max<int64_t>(1, ix.n_nonempty));
@@ -227,7 +281,7 @@ void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t*
     float* d1 = reinterpret_cast<float*>(w + l.d1);
     float* d2 = reinterpret_cast<float*>(w + l.d2);
     float* lut = (scan && uses_lut(scorer)) ? reinterpret_cast<float*>(w + l.lut) : nullptr;
-    launch_query_tables(ix, qc, nc, d1, d2, lut, st);
+    launch_query_tables(ix, qc, nc, d1, d2, lut, st, reinterpret_cast<int32_t*>(w + l.status));
     TraverseArgs ta{};
     ta.d1 = d1;
     ta.d2 = d2;
@@ -259,6 +313,38 @@ void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t*
     if (!scan) continue;
     ScanArgs sa = scan_args(ix, qc, nc, lut, ta.cells, ta.ncells, ta.cap, k, out_ids + c0 * k,
                             out_dists + c0 * k, reinterpret_cast<int32_t*>(w + l.qcounter));
+    if (hb) {
+      // per-(query, visited half-cell) tables on the tensor cores, then the M-lookup scan
+      HbpqArgs h{};
+      h.cells = ta.cells;
+      h.ncells = ta.ncells;
+      h.cap = ta.cap;
+      h.nq = nc;
+      h.T = ix.p.T;
+      h.M = ix.p.M;
+      h.D = ix.p.D;
+      h.queries = qc;
+      h.qbase = reinterpret_cast<int32_t*>(w + l.hb_qbase);
+      h.qrows = reinterpret_cast<int32_t*>(w + l.hb_qrows);
+      h.qbits = reinterpret_cast<uint32_t*>(w + l.hb_qbits);
+      h.hmap = reinterpret_cast<uint32_t*>(w + l.hb_hmap);
+      h.slot_counter = reinterpret_cast<unsigned long long*>(w + l.hb_ctr);
+      h.fb_count = reinterpret_cast<int32_t*>(w + l.hb_ctr + 8);
+      h.fallback = reinterpret_cast<int32_t*>(w + l.hb_fb);
+      h.slot_cap = l.hb_slots;
+      h.tables = reinterpret_cast<float*>(w + l.hb_tab);
+      h.status = reinterpret_cast<int32_t*>(w + l.status);
+      BPQ_CUDA(cudaMemsetAsync(w + l.hb_hmap, 0, (size_t)2 * ix.p.T * ((nc + 31) / 32) * 4, st));
+      BPQ_CUDA(cudaMemsetAsync(w + l.hb_ctr, 0, 16, st));
+      launch_hbpq_pairs(h, st);
+      launch_hbpq_tables(ix, h, st);
+      sa.hb_qbase = h.qbase;
+      sa.hb_qrows = h.qrows;
+      sa.hb_qbits = h.qbits;
+      sa.hb_tables = h.tables;
+      sa.qlist = h.fallback;
+      sa.qlist_n = h.fb_count;
+    }
     launch_scan(sa, scorer, st);
   }
 }
@@ -460,6 +546,7 @@ bpq_index* load_file(const char* path, int device) {
     ix->n_nonempty = nonempty;
     ix->max_cell = maxc;
     build_fbpq_tables(*ix, 0);
+    build_hbpq_tables(*ix, 0);
     build_point_cross(*ix, 0);
     BPQ_CUDA(cudaDeviceSynchronize());
   } catch (...) {
@@ -499,6 +586,7 @@ int bpq_create(bpq_index** out, const bpq_params* p, const float* C1_host, const
         BPQ_CUDA(cudaMemcpy(ix->S.p, S_host, cb_floats_local(*p) * 4, cudaMemcpyHostToDevice));
       }
       build_fbpq_tables(*ix, 0);
+      build_hbpq_tables(*ix, 0);
       empty_lists(*ix, 0);
       BPQ_CUDA(cudaDeviceSynchronize());
     } catch (...) {
@@ -525,6 +613,7 @@ int bpq_train_load(bpq_index** out, const bpq_params* p, const float* learn_dev,
       cudaStream_t st = static_cast<cudaStream_t>(stream);
       train_codebooks(*ix, learn_dev, n_learn, st);
       build_fbpq_tables(*ix, st);
+      build_hbpq_tables(*ix, st);
       empty_lists(*ix, st);
       BPQ_CUDA(cudaStreamSynchronize(st));
     } catch (...) {
@@ -618,9 +707,8 @@ int bpq_query_tables(const bpq_index* ix, const float* q, int64_t nq, float* d1,
 }
 
 size_t bpq_search_workspace_size(const bpq_index* ix, int64_t nq, int64_t L_max, int32_t k, int32_t scorer) {
-  (void)k;
   if (!ix || nq < 0 || L_max < 1) return 0;
-  return layout(*ix, std::max<int64_t>(nq, 1), L_max, scorer, true).total;
+  return layout(*ix, std::max<int64_t>(nq, 1), L_max, scorer, true, k).total;
 }
 
 int bpq_traverse(const bpq_index* ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride,
@@ -692,7 +780,9 @@ int bpq_search_status(const bpq_index* ix, void* ws, void* stream) {
     int32_t s = 0;
     BPQ_CUDA(cudaMemcpyAsync(&s, ws, 4, cudaMemcpyDeviceToHost, st));  // status is the first word
     BPQ_CUDA(cudaStreamSynchronize(st));
-    BPQ_CHECK(s == 0, BPQ_ECAPACITY, "a query overflowed a fixed-size buffer (band or cell list)");
+    BPQ_CHECK((s & STATUS_TIMEOUT) == 0, BPQ_ETIMEOUT,
+              "a bounded wait on a tensor-core table tile gave up (the tile was recomputed on the CUDA cores)");
+    BPQ_CHECK((s & STATUS_OVERFLOW) == 0, BPQ_ECAPACITY, "a query overflowed a fixed-size buffer (band or cell list)");
   });
 }
 
@@ -706,8 +796,8 @@ int bpq_search_host(bpq_index* ix, const float* q_host, int64_t nq, const int64_
     DeviceGuard dg(ix->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t L_max = read_L(L_host, L_stride, nq, nullptr);
-    const size_t want = std::min<size_t>(layout(*ix, nq, L_max, scorer, true).total, (size_t)4 << 30);
-    const size_t one = layout(*ix, 1, L_max, scorer, true).total;
+    const size_t want = std::min<size_t>(layout(*ix, nq, L_max, scorer, true, k).total, (size_t)4 << 30);
+    const size_t one = layout(*ix, 1, L_max, scorer, true, k).total;
     ix->host_ws.ensure(std::max(want, one));
     ix->host_q.ensure((size_t)nq * ix->p.D * 4);
     ix->host_ids.ensure((size_t)nq * k * 4);
@@ -718,6 +808,15 @@ int bpq_search_host(bpq_index* ix, const float* q_host, int64_t nq, const int64_
     BPQ_CUDA(cudaMemcpyAsync(ids_host, ix->host_ids.p, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));
     BPQ_CUDA(cudaMemcpyAsync(dists_host, ix->host_dists.p, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));
     BPQ_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+int bpq_set_hbpq_table_budget(bpq_index* ix, double slots_per_query) {
+  return guard([&] {
+    BPQ_CHECK(ix, BPQ_EINVAL, "index is NULL");
+    BPQ_CHECK(std::isfinite(slots_per_query) && slots_per_query >= 0.0, BPQ_EINVAL,
+              "slots per query must be finite and >= 0");
+    ix->hb_slots_per_query = slots_per_query;
   });
 }
 
@@ -732,7 +831,8 @@ int bpq_get_info(const bpq_index* ix, bpq_info* out) {
                                   ix->X1.bytes + ix->X2.bytes + ix->offsets.bytes + ix->codes.bytes +
                                   ix->ids.bytes + ix->cross.bytes + ix->pend_cells.bytes + ix->pend_codes.bytes +
                                   ix->pend_ids.bytes + ix->C1b.bytes + ix->C2b.bytes + ix->Rb.bytes + ix->n1.bytes +
-                                  ix->n2.bytes + ix->nR.bytes);
+                                  ix->n2.bytes + ix->nR.bytes + ix->Qb.bytes + ix->Sb.bytes + ix->E1.bytes +
+                                  ix->E2.bytes);
     out->params = ix->p;
   });
 }

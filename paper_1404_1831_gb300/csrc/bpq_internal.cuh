@@ -129,6 +129,34 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // ---------------------------------------------------------------------------
+// Tensor-core operand layout (tcgen05): operands K-major in shared memory without
+// swizzle, as 8-row x 16-byte core matrices; core (row group g, column group c) at
+// byte 128 (g * KB + c), KB = K / 8 column groups.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t core_off(int r, int k, int KB) {
+  return (uint32_t)((((r >> 3) * KB + (k >> 3)) * 128) + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (row-group)
+// byte offsets, the fixed 0b001 at bits 46-48, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Bounded wait on phase `parity` of an mbarrier: 1 when the phase completed,
+// 0 when `iters` polls went by first.
+__device__ __forceinline__ uint32_t mbar_wait_bounded(uint64_t* mbar, uint32_t parity, int iters) {
+  uint32_t ready = 0;
+  for (int it = 0; it < iters && !ready; ++it)
+    asm volatile("{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\nselp.u32 %0, 1, 0, P;\n}\n"
+                 : "=r"(ready) : "r"(smem_u32(mbar)), "r"(parity));
+  return ready;
+}
+
+// ---------------------------------------------------------------------------
 // Index object (host side).
 // ---------------------------------------------------------------------------
 struct DevBuf {
@@ -183,6 +211,13 @@ struct bpq_index {
   bpq::DevBuf C1b, C2b, Rb, n1, n2, nR;
   int kh = 0, ks = 0;
   bool coarse_bf16_exact = false, R_bf16_exact = false;
+  // HBPQ table form (local variant): BF16 copies of the local codebooks Q, S
+  // (T x M/2 x 256 x ks, K padded with zeros) and the query-independent part of
+  // the per-half-cell tables, E1[i][k][t] = ||Q^i_k[t]||^2 + 2<c^1_i|k, Q^i_k[t]>
+  // and E2 likewise with S^j, c^2_j (T x M/2 x 256 FP32 each)
+  bpq::DevBuf Qb, Sb, E1, E2;
+  bool local_bf16_exact = false;
+  double hb_slots_per_query = 0.0;  // 0: automatic (bpq_set_hbpq_table_budget)
   int64_t n_points = 0, n_nonempty = 0, max_cell = 0;
   // workspace owned by bpq_search_host
   bpq::DevBuf host_ws, host_q, host_ids, host_dists;
@@ -195,9 +230,42 @@ namespace bpq {
 // ---------------------------------------------------------------------------
 
 // Query tables (bpq_tables.cu).
+// status: workspace status word (may be NULL); a tensor-core tile whose bounded
+// wait gave up sets STATUS_TIMEOUT there and is recomputed on the CUDA cores.
 void launch_query_tables(const bpq_index& ix, const float* q, int64_t nq, float* d1, float* d2,
-                         float* lut, cudaStream_t st);
+                         float* lut, cudaStream_t st, int32_t* status = nullptr);
 void build_fbpq_tables(bpq_index& ix, cudaStream_t st);
+
+// Bits of the workspace status word.
+constexpr int32_t STATUS_OVERFLOW = 1;  // a fixed-size buffer (traversal band) overflowed
+constexpr int32_t STATUS_TIMEOUT = 2;   // a bounded device wait gave up
+
+// HBPQ table form (bpq_hbpq.cu).
+void build_hbpq_tables(bpq_index& ix, cudaStream_t st);
+bool hbpq_tensor_shape(const bpq_index& ix);  // the tensor-core table kernel covers (D, M)
+struct HbpqArgs {
+  const bpq_cell* cells;
+  const int32_t* ncells;
+  int32_t cap;
+  int64_t nq;
+  int32_t T, M, D;
+  const float* queries;   // nq x D
+  // per query: first table slot (-1: did not fit, scored by the fallback), number of
+  // distinct rows, and the row / column bitmaps (2 x ceil(T/32) words)
+  int32_t* qbase;
+  int32_t* qrows;
+  uint32_t* qbits;
+  // per half and half-cell: bitmap of the visiting queries (2 x T x ceil(nq/32) words, zeroed)
+  uint32_t* hmap;
+  unsigned long long* slot_counter;  // table slots taken (zeroed)
+  int32_t* fb_count;      // queries handed to the fallback (zeroed)
+  int32_t* fallback;      // nq: queries whose tables did not fit
+  int64_t slot_cap;       // table slots in `tables`
+  float* tables;          // slot_cap x M/2 x 256
+  int32_t* status;
+};
+void launch_hbpq_pairs(const HbpqArgs& h, cudaStream_t st);
+void launch_hbpq_tables(const bpq_index& ix, const HbpqArgs& h, cudaStream_t st);
 
 // Traversal (bpq_traverse.cu).
 struct TraverseArgs {
@@ -249,6 +317,14 @@ struct ScanArgs {
   const uint16_t* lut16;   // nq x M x 256 (fp16 form)
   const float* lut_scale;  // nq
   uint64_t* sl_out;        // nq x k
+  // HBPQ table form: per-query slots and bitmaps (HbpqArgs) and the tables
+  const int32_t* hb_qbase;
+  const int32_t* hb_qrows;
+  const uint32_t* hb_qbits;
+  const float* hb_tables;
+  // reconstruction scans: when set, only the queries qlist[0 .. *qlist_n) are scored
+  const int32_t* qlist;
+  const int32_t* qlist_n;
 };
 void launch_scan(const ScanArgs& a, int scorer, cudaStream_t st);
 // Shortlist scan with the int8 (f16 = false) or FP16 table: sl_out[q][0..k) =

@@ -721,17 +721,27 @@ __device__ uint32_t block_cut(const uint64_t* a, int n, int k, int* red) {
   return (uint32_t)hi;
 }
 
-template <int M, int NT, int D, int U, int KW, int CH>
+// HB = true: the same scan for HBPQ's table form (§3.2): a candidate of cell (i, j)
+// costs the M lookups key(i, j) + sum_k A_i[k][c_k] + sum_k B_j[k][c_{M/2+k}] into
+// the per-(query, half-cell) tables built by the HBPQ table kernel (read through
+// the cache from global memory; the table slots of the query come from its row
+// and column bitmaps), and no cross term is read.
+template <int M, int NT, int D, int U, int KW, int CH, bool HB>
 __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
-  constexpr int NW = NT / 32, R = CH / NT;
+  constexpr int NW = NT / 32, R = CH / NT, M2 = M / 2;
   static_assert(CH % NT == 0 && KW == 256, "shape (the exact prune keeps its payloads in the warp's 256 counters)");
+  constexpr int AREA0 = HB ? NW * KW * 8 : M * KSUB * 4;  // the query's table (FBPQ) or the final list (HB)
+  constexpr int TWMAX = MAX_T / 32;
   using CV = CodeVec<M>;
   extern __shared__ __align__(16) unsigned char smem[];
-  float* lut = reinterpret_cast<float*>(smem);                    // M x 256
-  uint64_t* wbuf = reinterpret_cast<uint64_t*>(lut + M * KSUB);   // NW x KW
+  float* lut = reinterpret_cast<float*>(smem);                    // M x 256 (FBPQ)
+  uint32_t* hbits = reinterpret_cast<uint32_t*>(smem + AREA0);    // HB: 2 x TWMAX row / column bitmap words
+  int* hpre = reinterpret_cast<int*>(hbits + (HB ? 2 * TWMAX : 0));  // HB: 2 x TWMAX bits below each word
+  uint64_t* wbuf = reinterpret_cast<uint64_t*>(hpre + (HB ? 2 * TWMAX : 0));  // NW x KW
   uint32_t* whist = reinterpret_cast<uint32_t*>(wbuf + NW * KW);  // NW x 256
   int2* c_info = reinterpret_cast<int2*>(whist + NW * 256);       // CH: (begin - first candidate, key bits)
   int* c_pref = reinterpret_cast<int*>(c_info + CH);              // CH + 1: first candidate of each cell
+  uint2* c_tab = reinterpret_cast<uint2*>(c_pref + CH + 2);       // HB, CH: table offsets (A_i, B_j) in floats
   __shared__ int scan_tmp[NW + 1];
   __shared__ int cut_red[2 * NW];
   __shared__ int fcount;
@@ -744,7 +754,22 @@ __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
 
   for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
     __syncthreads();  // the previous query's final list (in the table area) is written out
-    {
+    int hb_base = 0, hb_rows = 0, TW = 0;
+    if constexpr (HB) {
+      hb_base = a.hb_qbase[q];
+      if (hb_base < 0) continue;  // its tables did not fit: scored by the reconstruction fallback
+      hb_rows = a.hb_qrows[q];
+      TW = (a.T + 31) >> 5;
+      const uint32_t* qb = a.hb_qbits + q * 2 * TW;
+      for (int x = threadIdx.x; x < 2 * TW; x += NT) hbits[x] = qb[x];
+      __syncthreads();
+      for (int x = threadIdx.x; x < 2 * TW; x += NT) {
+        const int h0 = x >= TW ? TW : 0;
+        int p = 0;
+        for (int y = h0; y < x; ++y) p += __popc(hbits[y]);
+        hpre[x] = p;
+      }
+    } else {
       const float4* src = reinterpret_cast<const float4*>(a.lut + q * M * KSUB);
       for (int t = threadIdx.x; t < M * KSUB / 4; t += NT) reinterpret_cast<float4*>(lut)[t] = src[t];
     }
@@ -772,6 +797,13 @@ __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
           const bpq_cell cc = cl[cs + t];
           c_pref[t] = run;
           c_info[t] = make_int2((int)cc.begin - run, __float_as_int(cc.key));
+          if constexpr (HB) {
+            const uint32_t i = cc.cell / (uint32_t)a.T, j = cc.cell - i * (uint32_t)a.T;
+            const int ri = hpre[i >> 5] + __popc(hbits[i >> 5] & ((1u << (i & 31)) - 1u));
+            const int rj = hpre[TW + (j >> 5)] + __popc(hbits[TW + (j >> 5)] & ((1u << (j & 31)) - 1u));
+            c_tab[t] = make_uint2((uint32_t)(hb_base + ri) * (uint32_t)(M2 * KSUB),
+                                  (uint32_t)(hb_base + hb_rows + rj) * (uint32_t)(M2 * KSUB));
+          }
           run += (int)cc.count;
         }
       }
@@ -785,6 +817,7 @@ __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
         const unsigned le = (2u << lane) - 1u;
         uint32_t spos[D][U];
         float skey[D][U], sx[D][U];
+        int scl[D][U];
         CV scode[D][U];
         // a step: candidates f + 32u + lane (u < U); the cell starts that fall in
         // half h of the window [f, f + 32U) set bits of msk[h]
@@ -809,12 +842,16 @@ __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
               const unsigned msk = __reduce_or_sync(0xffffffffu, bits[h]);
               const int fl = f + 32 * h + lane;
               if (fl < e) {
-                const int2 inf = c_info[below + __popc(msk & le)];
+                const int cell = below + __popc(msk & le);
+                const int2 inf = c_info[cell];
                 const uint32_t pos = (uint32_t)(fl + inf.x);
                 spos[d][h] = pos;
                 skey[d][h] = __int_as_float(inf.y);
                 scode[d][h] = __ldg(reinterpret_cast<const CV*>(a.codes) + pos);
-                sx[d][h] = __ldg(a.cross + pos);
+                if constexpr (HB)
+                  scl[d][h] = cell;
+                else
+                  sx[d][h] = __ldg(a.cross + pos);
               }
               below += __popc(msk);
             }
@@ -836,7 +873,7 @@ __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
               acc[u] = false;
               o[u] = 0;
               if (spos[d][u] != NO_POS) {
-                float part = sx[d][u];
+                float part = HB ? 0.f : sx[d][u];
                 uint32_t wd[M / 4];
                 if constexpr (M == 16) {
                   wd[0] = scode[d][u].x;
@@ -847,10 +884,19 @@ __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
                   wd[0] = scode[d][u].x;
                   wd[1] = scode[d][u].y;
                 }
+                if constexpr (HB) {
+                  const uint2 tb = c_tab[scl[d][u]];
 #pragma unroll
-                for (int kk = 0; kk < M; ++kk) {
-                  const uint32_t off = ((wd[kk >> 2] >> (8 * (kk & 3))) & 0xffu) << 2;
-                  part += *reinterpret_cast<const float*>(lutb + kk * (KSUB * 4) + off);
+                  for (int kk = 0; kk < M; ++kk) {
+                    const uint32_t c = (wd[kk >> 2] >> (8 * (kk & 3))) & 0xffu;
+                    part += __ldg(a.hb_tables + (kk < M2 ? tb.x : tb.y) + (kk % M2) * KSUB + c);
+                  }
+                } else {
+#pragma unroll
+                  for (int kk = 0; kk < M; ++kk) {
+                    const uint32_t off = ((wd[kk >> 2] >> (8 * (kk & 3))) & 0xffu) << 2;
+                    part += *reinterpret_cast<const float*>(lutb + kk * (KSUB * 4) + off);
+                  }
                 }
                 o[u] = f2ord(skey[d][u] + part);
                 acc[u] = o[u] <= th_hi;
@@ -876,7 +922,7 @@ __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
     // final: the entries within the block threshold are gathered into the table
     // area (it holds every buffer), cut near the k best distances, given their
     // ids (read only here) and ranked exactly by (distance, id)
-    static_assert(NW * KW <= M * KSUB * 4 / 8, "the table area holds every buffered entry");
+    static_assert(NW * KW * 8 <= AREA0, "the table area holds every buffered entry");
     __syncthreads();
     const uint32_t th_hi = (uint32_t)(thr >> 32);
     int mine = 0;
@@ -1006,7 +1052,10 @@ __global__ void __launch_bounds__(NW * 32) recon_scan_kernel(ScanArgs a) {
   }
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) q_s = atomicAdd(a.qcounter, 1);
+    if (threadIdx.x == 0) {
+      const int64_t t = atomicAdd(a.qcounter, 1);
+      q_s = a.qlist ? (t < *a.qlist_n ? (int64_t)a.qlist[t] : a.nq) : t;
+    }
     __syncthreads();
     const int64_t q = q_s;
     if (q >= a.nq) break;
@@ -1113,12 +1162,13 @@ void run_fbpq_cfg(const ScanArgs& a, cudaStream_t st) {
   check_launch("fbpq scan kernel");
 }
 
-template <int M, int NT, int D, int U, int KW, int CH>
+template <int M, int NT, int D, int U, int KW, int CH, bool HB = false>
 void run_fbpq_seg(const ScanArgs& a, cudaStream_t st) {
   constexpr int NW = NT / 32;
-  const size_t smem = (size_t)M * KSUB * 4 + (size_t)NW * KW * 8 + (size_t)NW * 256 * 4 + (size_t)CH * 8 +
-                      (size_t)(CH + 1) * 4;
-  auto kern = fbpq_scan_seg_kernel<M, NT, D, U, KW, CH>;
+  const size_t smem = (HB ? (size_t)NW * KW * 8 + 4 * (MAX_T / 32) * 4 : (size_t)M * KSUB * 4) +
+                      (size_t)NW * KW * 8 + (size_t)NW * 256 * 4 + (size_t)CH * 8 + (size_t)(CH + 2) * 4 +
+                      (HB ? (size_t)CH * 8 : 0);
+  auto kern = fbpq_scan_seg_kernel<M, NT, D, U, KW, CH, HB>;
   BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
   kern<<<grid, NT, smem, st>>>(a);
@@ -1154,16 +1204,28 @@ void run_recon(const ScanArgs& a, cudaStream_t st) {
   check_launch("reconstruction scan kernel");
 }
 
+// HBPQ: with the per-half-cell tables of the batch (a.hb_tables, k <= 128) the
+// warp-segment scan with M lookups per candidate, then the O(D) reconstruction
+// scan for the queries listed in a.qlist (their tables did not fit); without
+// tables, the O(D) reconstruction for every query.
 template <int M, int SUB, int KP>
 void dispatch_scorer(const ScanArgs& a, int scorer, cudaStream_t st) {
-  if (scorer == BPQ_SCORER_FBPQ)
+  if (scorer == BPQ_SCORER_FBPQ) {
     run_fbpq<M, FB_POINT>(a, st);
-  else if (scorer == BPQ_SCORER_FBPQ_TABLES)
+  } else if (scorer == BPQ_SCORER_FBPQ_TABLES) {
     run_fbpq<M, FB_TABLES>(a, st);
-  else if (scorer == BPQ_SCORER_RECON)
+  } else if (scorer == BPQ_SCORER_RECON) {
     run_recon<M, SUB, KP, false>(a, st);
-  else
+  } else if (scorer == BPQ_SCORER_HBPQ && a.hb_tables) {
+    BPQ_CHECK(a.k <= 128 && a.qlist && a.qlist_n, BPQ_EINVAL, "HBPQ table scan: k <= 128 and a fallback list");
+    run_fbpq_seg<M, 128, 1, 4, 256, 512, true>(a, st);
     run_recon<M, SUB, KP, true>(a, st);
+  } else {
+    ScanArgs b = a;
+    b.qlist = nullptr;
+    b.qlist_n = nullptr;
+    run_recon<M, SUB, KP, true>(b, st);
+  }
 }
 
 template <int M, int SUB>

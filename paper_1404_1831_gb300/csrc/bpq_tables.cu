@@ -52,22 +52,9 @@ struct TcProblems {
   TcProblem p[MAXP];
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint32_t core_off(int r, int k, int KB) {
-  return (uint32_t)((((r >> 3) * KB + (k >> 3)) * 128) + (r & 7) * 16 + (k & 7) * 2);
-}
-
-// Shared-memory matrix descriptor: start, leading (K) and stride (row-group)
-// byte offsets, the fixed 0b001 at bits 46-48, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
-}
-
 template <int MODE>
 __global__ void __launch_bounds__(128) tc_table_kernel(const float* __restrict__ A, int lda, int na,
-                                                       TcProblems probs) {
+                                                       TcProblems probs, int32_t* status) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
@@ -145,11 +132,15 @@ __global__ void __launch_bounds__(128) tc_table_kernel(const float* __restrict__
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar)));
     }
-    uint32_t ready = 0;
-    for (int it = 0; it < (1 << 24) && !ready; ++it)  // bounded: an MMA group takes microseconds
-      asm volatile("{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\nselp.u32 %0, 1, 0, P;\n}\n"
-                   : "=r"(ready) : "r"(smem_u32(&mbar)), "r"(0));
-    done = __syncthreads_and(ready);
+    // bounded: an MMA group takes microseconds
+    done = __syncthreads_and(mbar_wait_bounded(&mbar, 0, 1 << 24));
+    if (!done) {
+      // the wait gave up: report it, and give the MMA a second bounded wait before
+      // the tensor memory it writes is released; the tile is then recomputed on
+      // the CUDA cores below
+      if (tid == 0 && status) atomicOr(status, STATUS_TIMEOUT);
+      __syncthreads_and(mbar_wait_bounded(&mbar, 0, 1 << 24));
+    }
     if (done) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       float an = 0.f;
@@ -317,7 +308,7 @@ void launch_quant_lut(const float* lut, int M, int64_t nq, void* out, float* sca
 }
 
 void launch_query_tables(const bpq_index& ix, const float* q, int64_t nq, float* d1, float* d2,
-                         float* lut, cudaStream_t st) {
+                         float* lut, cudaStream_t st, int32_t* status) {
   if (nq <= 0) return;
   const int D = ix.p.D, T = ix.p.T, M = ix.p.M;
   const int ty = (int)((nq + TC_M - 1) / TC_M);
@@ -335,7 +326,7 @@ void launch_query_tables(const bpq_index& ix, const float* q, int64_t nq, float*
     const size_t smem = (size_t)(TC_M + TC_N) * ix.kh * 2;
     BPQ_CUDA(cudaFuncSetAttribute(tc_table_kernel<MODE_SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((T + TC_N - 1) / TC_N, ty, np);
-    tc_table_kernel<MODE_SQ><<<grid, 128, smem, st>>>(q, D, (int)nq, pp);
+    tc_table_kernel<MODE_SQ><<<grid, 128, smem, st>>>(q, D, (int)nq, pp, status);
     check_launch("coarse table kernel");
   }
   if (lut) {
@@ -348,7 +339,7 @@ void launch_query_tables(const bpq_index& ix, const float* q, int64_t nq, float*
     const size_t smem = (size_t)(TC_M + TC_N) * ix.ks * 2;
     BPQ_CUDA(cudaFuncSetAttribute(tc_table_kernel<MODE_LUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(1, ty, M);
-    tc_table_kernel<MODE_LUT><<<grid, 128, smem, st>>>(q, D, (int)nq, pp);
+    tc_table_kernel<MODE_LUT><<<grid, 128, smem, st>>>(q, D, (int)nq, pp, status);
     check_launch("pq table kernel");
   }
 }

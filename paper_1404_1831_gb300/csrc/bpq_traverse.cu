@@ -782,7 +782,7 @@ __global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a, int onl
     if (threadIdx.x == 0) {
       a.ncells[q] = overflow ? -1 : nout;
       a.npoints[q] = committed;
-      if (overflow) atomicExch(a.status, 1);
+      if (overflow) atomicOr(a.status, STATUS_OVERFLOW);
     }
   }
 }
@@ -1182,7 +1182,7 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
       } else {
         a.ncells[q] = overflow ? -1 : nout;
         a.npoints[q] = committed;
-        if (overflow) atomicExch(a.status, 1);
+        if (overflow) atomicOr(a.status, STATUS_OVERFLOW);
       }
     }
   }

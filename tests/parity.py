@@ -11,7 +11,8 @@ def close(gpu, ora, rtol=RTOL):
     ora = np.asarray(ora, np.float64)
     both_inf = np.isinf(gpu) & np.isinf(ora)
     tol = rtol * np.maximum(np.abs(np.where(np.isinf(ora), 0, ora)), 1.0)
-    return both_inf | (np.abs(np.where(both_inf, 0, gpu - ora)) <= tol)
+    diff = np.where(both_inf, 0.0, gpu) - np.where(both_inf, 0.0, ora)
+    return both_inf | (np.abs(diff) <= tol)
 
 
 def assert_topk_match(g_ids, g_d, o_ids, o_d, rtol=RTOL):

@@ -46,3 +46,70 @@ def test_hbpq_search_matches_oracle(hbpq, tiny_oracle):
     ids, d = hbpq["ix"].search(q, 4000, 50, "hbpq")
     o_ids, o_d, _ = O.search(hbpq["oix"], qn, 4000, 50, "hbpq")
     assert assert_topk_match(ids.cpu().numpy(), d.cpu().numpy(), o_ids, o_d) == len(qn)
+
+
+def search_both(hbpq, qn, L, k, scorer="hbpq"):
+    q = torch.as_tensor(qn, dtype=torch.float32, device=DEV)
+    ids, d = hbpq["ix"].search(q, L, k, scorer)
+    hbpq["ix"].search_status()
+    o_ids, o_d, _ = O.search(hbpq["oix"], qn, L, k, "hbpq_tables")
+    return ids.cpu().numpy(), d.cpu().numpy(), o_ids, o_d
+
+
+@pytest.mark.parametrize("L", [1, 300, 4000, 40_000])
+@pytest.mark.parametrize("k", [1, 37, 128])
+def test_hbpq_table_form_matches_oracle(hbpq, tiny_oracle, L, k):
+    """Per-(query, half-cell) tables on the tensor cores + M-lookup scan (§3.2 regrouped):
+    identical top-k to the oracle's table form (itself pinned equal to the O(D)
+    reconstruction), from a single cell (L = 1) to every cell of the index."""
+    qn = tiny_oracle["queries"][:24]
+    ids, d, o_ids, o_d = search_both(hbpq, qn, L, k)
+    assert assert_topk_match(ids, d, o_ids, o_d) == len(qn)
+
+
+def test_hbpq_uneven_budgets_and_reconstruction_scorer(hbpq, tiny_oracle):
+    """Per-query budgets in one batch; the table form equals the paper's O(D) form
+    (scorer hbpq_recon) bit for bit."""
+    qn = tiny_oracle["queries"][:60]
+    Ls = np.array([1, 10, 100, 1000, 10_000, 40_000] * 10, dtype=np.int64)
+    q = torch.as_tensor(qn, dtype=torch.float32, device=DEV)
+    a = [t.cpu().numpy() for t in hbpq["ix"].search(q, Ls, 100, "hbpq")]
+    b = [t.cpu().numpy() for t in hbpq["ix"].search(q, Ls, 100, "hbpq_recon")]
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    o_ids, o_d, _ = O.search(hbpq["oix"], qn, Ls, 100, "hbpq")
+    assert assert_topk_match(a[0], a[1], o_ids, o_d) == len(qn)
+
+
+def test_hbpq_large_k_uses_reconstruction(hbpq, tiny_oracle):
+    """k > 128 takes the O(D) scan: still identical to the oracle."""
+    qn = tiny_oracle["queries"][:10]
+    ids, d, o_ids, o_d = search_both(hbpq, qn, 4000, 300)
+    assert assert_topk_match(ids, d, o_ids, o_d) == len(qn)
+
+
+def test_hbpq_table_overflow_falls_back(hbpq, tiny_oracle):
+    """With a table budget too small for most queries, the queries that do not fit
+    are scored by the O(D) reconstruction scan: the answers do not change."""
+    qn = tiny_oracle["queries"][:32]
+    ix = hbpq["ix"]
+    ref = search_both(hbpq, qn, 20_000, 100)
+    try:
+        ix.set_hbpq_table_budget(3.0)  # 96 slots for 32 queries that need ~100 each
+        got = search_both(hbpq, qn, 20_000, 100)
+    finally:
+        ix.set_hbpq_table_budget(0.0)
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
+    assert assert_topk_match(got[0], got[1], got[2], got[3]) == len(qn)
+
+
+def test_hbpq_chunked_workspace(hbpq, tiny_oracle):
+    """A workspace for a few queries processes the batch in chunks, tables included."""
+    import paper_1404_1831_gb300 as bpq
+    qn = tiny_oracle["queries"][:40]
+    ix = hbpq["ix"]
+    q = torch.as_tensor(qn, dtype=torch.float32, device=DEV)
+    need = bpq.lib().bpq_search_workspace_size(ix._h, 3, 4000, 50, bpq.SCORERS["hbpq"])
+    ws = torch.empty(need, dtype=torch.uint8, device=DEV)
+    ids, d = ix.search(q, 4000, 50, "hbpq", workspace=ws)
+    o_ids, o_d, _ = O.search(hbpq["oix"], qn, 4000, 50, "hbpq")
+    assert assert_topk_match(ids.cpu().numpy(), d.cpu().numpy(), o_ids, o_d) == len(qn)
