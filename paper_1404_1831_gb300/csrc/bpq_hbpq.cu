@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(128) hbpq_table_kernel(TabArgs a) {
   unsigned char* sA = hsm;                     // HT_M * H * 2 bytes
   unsigned char* sB = sA + HT_M * H * 2;       // m2 x (256 x 16 BF16) = m2 x 8 KB
   float* Es = reinterpret_cast<float*>(sB + (a.tensor ? m2 * HT_N * 32 : 0));  // m2 x 256
+  float* stage = Es + m2 * KSUB + warp * (32 * 33);  // per warp: 32 rows x 32 columns (+1 pad)
   const float* E = a.E[half] + (int64_t)i * m2 * KSUB;
   for (int e = tid; e < m2 * KSUB; e += 128) Es[e] = E[e];
   bool tc = a.tensor != 0;
@@ -273,7 +274,6 @@ __global__ void __launch_bounds__(128) hbpq_table_kernel(TabArgs a) {
           }
           phase ^= 1u;
           asm volatile("tcgen05.fence::after_thread_sync;");
-          float* out = h.tables + (r < nt ? tslot[r] : 0) * (int64_t)(m2 * KSUB) + k * KSUB;
           for (int c0 = 0; c0 < HT_N; c0 += 32) {
             uint32_t v[32];
             asm volatile(
@@ -286,18 +286,27 @@ __global__ void __launch_bounds__(128) hbpq_table_kernel(TabArgs a) {
                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                 : "r"(tm + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (r < nt) {
-              const float* e = Es + k * KSUB + c0;
+            // lane = tile row: stage the 32 x 32 block, then write it row by row so
+            // that each store instruction covers four whole 128-byte rows
 #pragma unroll
-              for (int j = 0; j < 32; j += 4) {
+            for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(v[j]);
+            __syncwarp();
+            const float* e = Es + k * KSUB + c0 + (lane & 7) * 4;
+#pragma unroll
+            for (int rr = 0; rr < 32; rr += 4) {
+              const int row = rr + (lane >> 3), trow = warp * 32 + row;
+              if (trow < nt) {
+                const float* sv = stage + row * 33 + (lane & 7) * 4;
                 float4 o;
-                o.x = __fsub_rn(e[j], 2.f * __uint_as_float(v[j]));
-                o.y = __fsub_rn(e[j + 1], 2.f * __uint_as_float(v[j + 1]));
-                o.z = __fsub_rn(e[j + 2], 2.f * __uint_as_float(v[j + 2]));
-                o.w = __fsub_rn(e[j + 3], 2.f * __uint_as_float(v[j + 3]));
-                *reinterpret_cast<float4*>(out + c0 + j) = o;
+                o.x = __fsub_rn(e[0], 2.f * sv[0]);
+                o.y = __fsub_rn(e[1], 2.f * sv[1]);
+                o.z = __fsub_rn(e[2], 2.f * sv[2]);
+                o.w = __fsub_rn(e[3], 2.f * sv[3]);
+                *reinterpret_cast<float4*>(h.tables + tslot[trow] * (int64_t)(m2 * KSUB) + k * KSUB + c0 +
+                                           (lane & 7) * 4) = o;
               }
             }
+            __syncwarp();
           }
           // every lane's tensor-memory reads are complete before the next MMA writes
           asm volatile("tcgen05.fence::before_thread_sync;");
@@ -376,7 +385,8 @@ void launch_hbpq_tables(const bpq_index& ix, const HbpqArgs& h, cudaStream_t st)
   a.H = ix.h;
   a.tensor = (hbpq_tensor_shape(ix) && ix.local_bf16_exact && (ix.p.D & 3) == 0 &&
               (reinterpret_cast<uintptr_t>(h.queries) & 15) == 0) ? 1 : 0;
-  const size_t smem = (size_t)HT_M * ix.h * 2 + (a.tensor ? (size_t)ix.m2 * HT_N * 32 : 0) + (size_t)ix.m2 * KSUB * 4;
+  const size_t smem = (size_t)HT_M * ix.h * 2 + (a.tensor ? (size_t)ix.m2 * HT_N * 32 : 0) + (size_t)ix.m2 * KSUB * 4 +
+                      (size_t)4 * 32 * 33 * 4;
   BPQ_CHECK(smem <= 200 * 1024, BPQ_EINVAL, "HBPQ table kernel: shape too large for shared memory");
   BPQ_CUDA(cudaFuncSetAttribute(hbpq_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(h.T, 2);

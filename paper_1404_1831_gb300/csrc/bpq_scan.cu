@@ -727,10 +727,10 @@ __device__ uint32_t block_cut(const uint64_t* a, int n, int k, int* red) {
 // the cache from global memory; the table slots of the query come from its row
 // and column bitmaps), and no cross term is read.
 template <int M, int NT, int D, int U, int KW, int CH, bool HB>
-__global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
+__global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs a) {
   constexpr int NW = NT / 32, R = CH / NT, M2 = M / 2;
   static_assert(CH % NT == 0 && KW == 256, "shape (the exact prune keeps its payloads in the warp's 256 counters)");
-  constexpr int AREA0 = HB ? NW * KW * 8 : M * KSUB * 4;  // the query's table (FBPQ) or the final list (HB)
+  constexpr int AREA0 = HB ? 0 : M * KSUB * 4;  // the query's table (FBPQ)
   constexpr int TWMAX = MAX_T / 32;
   using CV = CodeVec<M>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -810,7 +810,12 @@ __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
       if (threadIdx.x == 0) c_pref[nch] = total;
       __syncthreads();
       const int P = total;
-      const int s = (int)(((long long)P * w) / NW), e = (int)(((long long)P * (w + 1)) / NW);
+      // FBPQ: each warp walks one contiguous quarter of the chunk.  HB: the warps
+      // take the windows of 32U candidates in turn, so the CTA's warps work in the
+      // same few cells at a time and their table lookups share the L1 cache.
+      constexpr int WSTEP = HB ? NW : 1;
+      const int s = HB ? 32 * U * w : (int)(((long long)P * w) / NW);
+      const int e = HB ? P : (int)(((long long)P * (w + 1)) / NW);
       if (s < e) {
         int c = find_cell(c_pref, nch, s);  // cell of the next step's first candidate
         int f = s;                          // next step's first candidate
@@ -825,6 +830,7 @@ __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
 #pragma unroll
           for (int u = 0; u < U; ++u) spos[d][u] = NO_POS;
           if (f < e) {
+            if constexpr (HB) c = find_cell(c_pref, nch, f);
             unsigned bits[U];
 #pragma unroll
             for (int h = 0; h < U; ++h) bits[h] = 0u;
@@ -857,12 +863,12 @@ __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
             }
             c = below;
             if (c + 1 <= nch && c_pref[c + 1] == f + 32 * U) ++c;
-            f += 32 * U;
+            f += 32 * U * WSTEP;
           }
         };
 #pragma unroll
         for (int d = 0; d < D; ++d) issue(d);
-        for (int left = (e - s + 32 * U - 1) / (32 * U); left > 0; left -= D) {
+        for (int left = (e - s + 32 * U * WSTEP - 1) / (32 * U * WSTEP); left > 0; left -= D) {
           const uint32_t th_hi = (uint32_t)(*(volatile unsigned long long*)&thr >> 32);
 #pragma unroll
           for (int d = 0; d < D; ++d) {
@@ -922,7 +928,8 @@ __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
     // final: the entries within the block threshold are gathered into the table
     // area (it holds every buffer), cut near the k best distances, given their
     // ids (read only here) and ranked exactly by (distance, id)
-    static_assert(NW * KW * 8 <= AREA0, "the table area holds every buffered entry");
+    static_assert(NW * KW * 8 <= (HB ? CH * 8 + (CH + 2) * 4 + CH * 8 : AREA0),
+                  "the final area holds every buffered entry");
     __syncthreads();
     const uint32_t th_hi = (uint32_t)(thr >> 32);
     int mine = 0;
@@ -939,7 +946,8 @@ __global__ void __launch_bounds__(NT, 8) fbpq_scan_seg_kernel(ScanArgs a) {
       base += (x < w) ? scan_tmp[x] : 0;
       n += scan_tmp[x];
     }
-    uint64_t* fin = reinterpret_cast<uint64_t*>(lut);  // the table is no longer read
+    // the table (FBPQ) or the chunk's cell arrays (HB) are no longer read
+    uint64_t* fin = HB ? reinterpret_cast<uint64_t*>(c_info) : reinterpret_cast<uint64_t*>(lut);
     for (int e0 = 0; e0 < wn; e0 += 32) {
       const int e = e0 + lane;
       const uint64_t x = e < wn ? wb[e] : EMPTY;
@@ -1165,11 +1173,13 @@ void run_fbpq_cfg(const ScanArgs& a, cudaStream_t st) {
 template <int M, int NT, int D, int U, int KW, int CH, bool HB = false>
 void run_fbpq_seg(const ScanArgs& a, cudaStream_t st) {
   constexpr int NW = NT / 32;
-  const size_t smem = (HB ? (size_t)NW * KW * 8 + 4 * (MAX_T / 32) * 4 : (size_t)M * KSUB * 4) +
+  const size_t smem = (HB ? (size_t)4 * (MAX_T / 32) * 4 : (size_t)M * KSUB * 4) +
                       (size_t)NW * KW * 8 + (size_t)NW * 256 * 4 + (size_t)CH * 8 + (size_t)(CH + 2) * 4 +
                       (HB ? (size_t)CH * 8 : 0);
   auto kern = fbpq_scan_seg_kernel<M, NT, D, U, KW, CH, HB>;
   BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // HB reads its tables through L1: shared memory for five CTAs (132 KB), the rest as cache
+  if (HB) BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 57));
   const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
   kern<<<grid, NT, smem, st>>>(a);
   check_launch("fbpq segment scan kernel");
