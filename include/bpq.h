@@ -305,7 +305,9 @@ int bpq_search_host(bpq_index* idx, const float* queries_host, int64_t nq, const
  *  GPU work (split the batch).  status_dev (may be NULL): one int32 of device
  *  memory that receives 0, or 1 if a query overflowed the traversal band.
  *  The first call on a device looks up the array's device address (one-time
- *  set-up), so make that first call before any stream capture.  Every call
+ *  set-up), so make that first call before any stream capture.  That address
+ *  belongs to the device's primary context: calls from another context of the
+ *  device, or after cudaDeviceReset, are not supported.  Every call
  *  shares the array and it keeps the previous call's contents; calls whose GPU
  *  work overlaps (other streams, other threads) race on it, so order them.
  *  Per-query budgets (L_stride == 1) are copied from host memory with

@@ -29,7 +29,10 @@ void* g_noalloc_ptr[MAX_DEVICES] = {};
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Device address of the scratch array on the current device.  Host code cannot
-// use the array's name as an address, so it is looked up once per device.
+// use the array's name as an address, so it is looked up once per device.  The
+// address belongs to the device's primary context (the one the CUDA runtime
+// uses); it is not valid in another context of the same device, nor after
+// cudaDeviceReset, and this entry point does not support either.
 void* scratch_address(int device) {
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   if (!g_noalloc_ptr[device]) {
@@ -167,6 +170,8 @@ extern "C" int bpq_search_noalloc(const bpq_index* ix, const float* queries_dev,
     if (status_dev) BPQ_CUDA(cudaMemcpyAsync(status_dev, w + o.status, 4, cudaMemcpyDeviceToDevice, st));
   } catch (const bpq::Error& e) {
     rc = e.code;
+  } catch (...) {  // nothing else may cross the C boundary (e.g. a failed mutex lock)
+    rc = BPQ_ECUDA;
   }
   if (prev >= 0 && prev != ix->device) cudaSetDevice(prev);
   return rc;

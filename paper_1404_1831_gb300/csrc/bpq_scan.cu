@@ -965,10 +965,10 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
     }
     __syncthreads();
     const int m = fcount;
-    for (int t = threadIdx.x; t < m; t += NT) {  // rank among the survivors (composites are distinct)
-      const uint64_t x = wbuf[t];
+    for (int t = threadIdx.x; t < m; t += NT) {  // rank among the survivors; equal composites (a
+      const uint64_t x = wbuf[t];                 // point added twice under one id) by position
       int r = 0;
-      for (int j = 0; j < m; ++j) r += (wbuf[j] < x) ? 1 : 0;
+      for (int j = 0; j < m; ++j) r += (wbuf[j] < x || (wbuf[j] == x && j < t)) ? 1 : 0;
       if (r < k) {
         a.out_ids[q * k + r] = (int32_t)(uint32_t)x;
         a.out_dists[q * k + r] = ord2f((uint32_t)(x >> 32));
