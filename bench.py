@@ -452,9 +452,12 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
 
 
-def serve_block(ix, w, mix, k, seconds, seed=11, n_max=300_000, max_batch=4096):
-    """Poisson stream with per-query L uniform over {1k, 10k, 100k}: latency p50 / p99 at 50 % and 80 %
-    of the saturated throughput of the same mix (full batches through the same host-buffer call)."""
+def serve_block(ix, w, mix, k, seconds, seed=11, n_max=300_000, max_batch=4096, slots=3, device_bytes=12 << 30):
+    """Poisson stream with per-query L uniform over {1k, 10k, 100k}, latency from arrival to results in host
+    memory.  Continuous batching (bpq_server: `slots` batches in flight on their own streams, admission by
+    device memory, one budget class per batch) at 50 % and 80 % of its saturated throughput (every query
+    queued at time zero), next to the blocking queue (one bpq_search_host call at a time) at the same
+    offered rates."""
     import numpy as np
 
     import synthdata as sd
@@ -463,15 +466,27 @@ def serve_block(ix, w, mix, k, seconds, seed=11, n_max=300_000, max_batch=4096):
     qh = sdev.points_cuda(mix, sd.STREAM_QUERY, w.n_query, n_max).cpu().numpy()  # after the timed batch
     mix_L = np.array([1_000, 10_000, 100_000], dtype=np.int64)
     Ls = mix_L[np.random.default_rng(seed).integers(0, len(mix_L), n_max)]
-    sat = serving.saturated_qps(ix, qh, Ls, k, batch=max_batch)
-    out = {"L_mix": mix_L.tolist(), "k": k, "max_batch": max_batch, "saturated_qps": sat,
-           "latency": "arrival to results in host memory (bpq_search_host: H2D, search, D2H)", "loads": {}}
+    n_sat = min(n_max, 60_000)
+    cfg = dict(k=k, slots=slots, max_batch=max_batch, L_max=int(mix_L.max()), device_bytes=device_bytes)
+    serving.serve_continuous(ix, qh[:4096], Ls[:4096], np.zeros(4096), **cfg)  # warm-up
+    sat = serving.serve_continuous(ix, qh[:n_sat], Ls[:n_sat], np.zeros(n_sat), **cfg)
+    sat_qps = n_sat / sat.wall_s
+    sat_queue = serving.saturated_qps(ix, qh, Ls, k, batch=max_batch)
+    out = {"L_mix": mix_L.tolist(), "k": k, "latency": "arrival to results in host memory (copies included)",
+           "continuous": {"slots": slots, "max_batch": max_batch, "device_bytes": device_bytes,
+                          "admission": "bpq_search_workspace_size of the batch at its largest L <= device_bytes / slots",
+                          "batching": "one budget class (floor(log2 L)) per batch, oldest class first",
+                          "saturated_qps": sat_qps, "saturated_stats": sat.stats, "loads": {}},
+           "queue": {"max_batch": max_batch, "saturated_qps": sat_queue, "loads": {}}}
     for load in (0.5, 0.8):
-        rate = load * sat
+        rate = load * sat_qps
         n = int(min(n_max, max(1000, rate * seconds)))
-        res = serving.serve(ix, qh[:n], Ls[:n], serving.poisson_arrivals(n, rate, seed + int(10 * load)), k,
-                            max_batch=max_batch)
-        out["loads"][f"{load:.1f}"] = {"offered_qps": rate, **res.summary()}
+        arr = serving.poisson_arrivals(n, rate, seed + int(10 * load))
+        res = serving.serve_continuous(ix, qh[:n], Ls[:n], arr, **cfg)
+        out["continuous"]["loads"][f"{load:.1f}"] = {"offered_qps": rate, **res.summary(),
+                                                     "max_in_flight": res.stats["max_in_flight"]}
+        res = serving.serve(ix, qh[:n], Ls[:n], arr, k, max_batch=max_batch)
+        out["queue"]["loads"][f"{load:.1f}"] = {"offered_qps": rate, **res.summary()}
     return out
 
 

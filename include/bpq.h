@@ -333,6 +333,74 @@ int bpq_search_noalloc(const bpq_index* idx, const float* queries_dev, int64_t n
  */
 int bpq_set_hbpq_table_budget(bpq_index* idx, double slots_per_query);
 
+/*
+ * Continuous-batching server: a request loop over one resident index (serving
+ * is not part of the paper, which measures one query at a time; every batch runs
+ * the bpq_search pipeline of §2.3.3 / §3.1 / §3.2 unchanged, so each query's
+ * answer equals bpq_search of that query alone).
+ *
+ * The server owns `slots` batches in flight, each with its own non-blocking CUDA
+ * stream, a device workspace of device_bytes / slots bytes, device and page-locked
+ * host buffers for max_batch queries, and a completion event.  Progress calls
+ * retire finished slots (their results are then in host memory) and fill free
+ * slots with batches of waiting requests, oldest first, enqueued asynchronously
+ * (H2D copy, search, D2H copy); batches therefore overlap on the GPU.  A batch
+ * admits requests only while bpq_search_workspace_size of the batch at its largest
+ * L fits the slot's workspace (admission by device memory), and with
+ * group_by_budget it takes requests of one budget class only (floor(log2 L)), so
+ * short queries do not wait for the long queries of their batch.
+ * A server is used from one host thread at a time; the index must outlive it and
+ * must not be modified while it exists.
+ */
+typedef struct bpq_server bpq_server;
+typedef struct {
+  int32_t slots;           /* batches in flight, 1..64 */
+  int32_t k;               /* results per query, 1..1024 */
+  int32_t scorer;          /* BPQ_SCORER_* (matching the index's variant) */
+  int32_t group_by_budget; /* 1: one budget class per batch; 0: first come first served */
+  int64_t max_batch;       /* queries per batch, 1..2^20 */
+  int64_t L_max;           /* the largest candidate budget a request may ask for */
+  size_t device_bytes;     /* device memory for all slots' workspaces */
+} bpq_server_config;
+typedef struct {
+  int64_t batches;         /* batches launched */
+  int64_t queries;         /* queries launched */
+  int64_t max_in_flight;   /* most batches in flight at once */
+  int64_t pending;         /* requests waiting for a slot */
+  int64_t slot_workspace_bytes;
+} bpq_server_stats;
+
+/* bpq_server_create — allocates the slots.  Errors: BPQ_EINVAL, BPQ_ESTATE
+ * (unfinalized index), BPQ_ECAPACITY (device_bytes / slots cannot hold one query at
+ * L_max), BPQ_ENOMEM, BPQ_ECUDA. */
+int bpq_server_create(bpq_server** out, const bpq_index* idx, const bpq_server_config* cfg);
+/* bpq_server_submit — queues n requests: queries_host n x D float32 (copied),
+ * L_host n budgets in [1, L_max]; request numbers first_request_out .. + n - 1
+ * (may be NULL).  Nothing is launched until bpq_server_progress. */
+int bpq_server_submit(bpq_server* s, const float* queries_host, const int64_t* L_host, int64_t n,
+                      int64_t* first_request_out);
+/* bpq_server_progress — retires finished batches and launches waiting requests
+ * into free slots.  wait != 0: if neither happened, blocks until one in-flight
+ * batch finishes, then launches again. */
+int bpq_server_progress(bpq_server* s, int32_t wait);
+/* bpq_server_take — up to max_n finished requests, in completion order:
+ * request numbers, ids / dists (max_n x k, as bpq_search), latency_s (may be NULL:
+ * seconds from submission to the progress call that saw the batch finish);
+ * *n_out = how many were written. */
+int bpq_server_take(bpq_server* s, int64_t max_n, int64_t* request_out, int32_t* ids_out, float* dists_out,
+                    double* latency_s_out, int64_t* n_out);
+/* bpq_server_run_trace — serves a recorded arrival trace: request i (queries_host
+ * row i, budget L_host[i]) arrives arrival_s[i] seconds (non-decreasing) after the
+ * call starts; the server admits arrived requests, launches and retires batches as
+ * above until all n are answered.  ids_out / dists_out: n x k rows in request
+ * order; latency_s_out[i]: arrival to results in host memory.  Needs an idle
+ * server.  Returns when every request is answered. */
+int bpq_server_run_trace(bpq_server* s, const float* queries_host, const int64_t* L_host, const double* arrival_s,
+                         int64_t n, int32_t* ids_out, float* dists_out, double* latency_s_out);
+int bpq_server_get_stats(const bpq_server* s, bpq_server_stats* out);
+/* bpq_server_free — waits for the slots' streams and releases the server (NULL is allowed). */
+void bpq_server_free(bpq_server* s);
+
 /* bpq_info / bpq_arrays — sizes and read-only device views (see the structs). */
 int bpq_get_info(const bpq_index* idx, bpq_info* out);
 int bpq_get_arrays(const bpq_index* idx, bpq_arrays* out);

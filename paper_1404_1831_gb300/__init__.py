@@ -43,6 +43,17 @@ class Arrays(ctypes.Structure):
                                                 "cross")]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("k", ctypes.c_int32), ("scorer", ctypes.c_int32),
+                ("group_by_budget", ctypes.c_int32), ("max_batch", ctypes.c_int64), ("L_max", ctypes.c_int64),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_int64), ("queries", ctypes.c_int64), ("max_in_flight", ctypes.c_int64),
+                ("pending", ctypes.c_int64), ("slot_workspace_bytes", ctypes.c_int64)]
+
+
 CELL_DTYPE = np.dtype([("cell", "<u4"), ("begin", "<u4"), ("count", "<u4"), ("key", "<f4")])
 
 # Every entry point of include/bpq.h, with its ctypes signature.
@@ -77,6 +88,13 @@ _SIGS = {
     "bpq_get_arrays": (ctypes.c_int, [_P, ctypes.POINTER(Arrays)]),
     "bpq_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "bpq_free": (None, [_P]),
+    "bpq_server_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, ctypes.POINTER(ServerConfig)]),
+    "bpq_server_submit": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P]),
+    "bpq_server_progress": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "bpq_server_take": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P, _P]),
+    "bpq_server_run_trace": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, _P, _P]),
+    "bpq_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
+    "bpq_server_free": (None, [_P]),
 }
 
 _LIB = None

@@ -224,11 +224,16 @@ void check_scorer(const bpq_index& ix, int scorer) {
     BPQ_CHECK(ix.p.variant == BPQ_VARIANT_GLOBAL, BPQ_EINVAL, "FBPQ and reconstruction scorers need global codebooks");
 }
 
+}  // namespace
+
 // Runs tables + traversal (+ scan when ids/dists are given) over the queries in
-// chunks that fit the workspace.
-void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride,
-                 int k, int scorer, int32_t* out_ids, float* out_dists, bpq_cell* user_cells, int32_t user_cap,
-                 int32_t* user_ncells, int64_t* user_npoints, void* ws, size_t ws_bytes, cudaStream_t st) {
+// chunks that fit the workspace.  L32_pinned (optional, per-query budgets only):
+// the same budgets as int32 in page-locked host memory, copied from there so that
+// no pageable copy stalls the host on the stream.
+void bpq::run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride,
+                      int k, int scorer, int32_t* out_ids, float* out_dists, bpq_cell* user_cells, int32_t user_cap,
+                      int32_t* user_ncells, int64_t* user_npoints, void* ws, size_t ws_bytes, cudaStream_t st,
+                      const int32_t* L32_pinned) {
   const bool scan = user_cells == nullptr;
   std::vector<int32_t> Lq;
   const int64_t L_max = read_L(L_host, L_stride, nq, &Lq);
@@ -287,7 +292,7 @@ void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t*
     ta.d2 = d2;
     ta.offsets = ix.offsets.as<uint32_t>();
     if (L_stride) {
-      BPQ_CUDA(cudaMemcpyAsync(w + l.L, Lq.data() + c0, nc * 4, cudaMemcpyHostToDevice, st));
+      BPQ_CUDA(cudaMemcpyAsync(w + l.L, (L32_pinned ? L32_pinned : Lq.data()) + c0, nc * 4, cudaMemcpyHostToDevice, st));
       ta.L = reinterpret_cast<const int32_t*>(w + l.L);
     } else {
       ta.L = nullptr;
@@ -348,6 +353,8 @@ void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t*
     launch_scan(sa, scorer, st);
   }
 }
+
+namespace {
 
 // ---------------------------------------------------------------------------
 // bpq_search_shortlist: the bpq_search layout plus the reduced-precision tables
@@ -557,6 +564,8 @@ bpq_index* load_file(const char* path, int device) {
 }
 
 }  // namespace
+
+void bpq::set_last_error(const std::string& msg) { g_last_error = msg; }
 
 extern "C" {
 

@@ -352,6 +352,15 @@ void launch_rescore(const RescoreArgs& r, cudaStream_t st);
 void launch_quant_lut(const float* lut, int M, int64_t nq, void* out, float* scale, bool f16, cudaStream_t st);
 bool scan_supported(int D, int M);  // (D, M) shapes the scan kernels are built for
 
+// Text returned by bpq_last_error on the calling thread (bpq_api.cu).
+void set_last_error(const std::string& msg);
+
+// The search pipeline of bpq_search / bpq_traverse (bpq_api.cu).
+void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride,
+                 int k, int scorer, int32_t* out_ids, float* out_dists, bpq_cell* user_cells, int32_t user_cap,
+                 int32_t* user_ncells, int64_t* user_npoints, void* ws, size_t ws_bytes, cudaStream_t st,
+                 const int32_t* L32_pinned = nullptr);
+
 // Index build (bpq_build.cu).
 void launch_encode(const bpq_index& ix, const float* x, int64_t n, int32_t* cell, uint8_t* codes,
                    cudaStream_t st);
