@@ -51,6 +51,7 @@ def parse_args():
     ap.add_argument("--no-sweep", action="store_true", help="skip the L / scorer sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the Poisson serving measurement")
+    ap.add_argument("--no-configs", action="store_true", help="skip the 100M / 1B configuration blocks")
     ap.add_argument("--workload", choices=("sift10m", "c3", "c4", "c5"), default="sift10m",
                     help="c3: 100M, M=16, int8 shortlist; c4: 100M, local codebooks, uneven L; "
                          "c5: 1B points, serving (each prints its own JSON line)")
@@ -440,8 +441,17 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
-    del ix
+    del ix, ws, tws, cells, flush
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_configs:
+        # the 100M and 1B configurations, each on a fresh index (outside the timed region)
+        out["configs"] = {}
+        for name in ("c3", "c4", "c5"):
+            t0 = time.time()
+            out["configs"][name] = config_block(name, args.serve_seconds)
+            out["configs"][name]["wall_s"] = round(time.time() - t0, 1)
+            torch.cuda.empty_cache()
     if want_cpu:
         res = run_oracle(w, L, k, args.oracle_seconds)
         out["cpu_baseline"] = {"value": res["n"] / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -541,21 +551,25 @@ def recall_of(ids, nn):
     return {f"R@{R}": float(hit[:, :R].any(1).float().mean()) for R in (1, 10, 100)}
 
 
-def run_config(args):
-    """The larger configurations: C3 (100M, M = 16: FP32 FBPQ vs the int8 and FP16 shortlists with
-    exact re-scoring at L = 30k), C4 (100M, local codebooks, L = round(10^U(3, 5)) per
-    query: HBPQ vs the global codebooks' FBPQ and reconstruction), C5 (1B points:
-    batch queries/s per L and Poisson serving latency)."""
+def config_block(name, serve_seconds=0.25):
+    """One of the larger configurations, measured on the GPU (returns a dict):
+      c3  100M points, M = 16, L = 30k: FP32 FBPQ vs the int8 and FP16 table shortlists (1000) with exact
+          re-scoring; identical-list fraction, recall;
+      c4  100M points, L = round(10^U(3, 5)) per query: HBPQ (tables on the tensor cores, and the O(D)
+          reconstruction) vs the global codebooks' FBPQ and reconstruction; recall;
+      c5  1B points: FBPQ batch queries/s at L = 1k / 10k / 100k, resident bytes of both FBPQ forms, and
+          continuous-batching serving latency.
+    Recall is against exact nearest neighbours by GPU brute force (1,000 queries).  Oracle parity at these
+    sizes is checked by the slow GPU tests, not here."""
     import numpy as np
     import torch
 
     import paper_1404_1831_gb300 as bpq
     import synthdata as sd
     from synthdata import device as sdev
-    torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     torch.backends.cuda.matmul.allow_tf32 = False
-    w = {"c3": sd.SIFT100M_M16, "c4": sd.SIFT100M, "c5": sd.SIFT1B}[args.workload]
+    w = {"c3": sd.SIFT100M_M16, "c4": sd.SIFT100M, "c5": sd.SIFT1B}[name]
     mix = sd.make_mixture(w.seed, w.n_comp)
     learn = sdev.points_cuda(mix, sd.STREAM_LEARN, 0, w.n_learn, device=dev)
 
@@ -588,14 +602,16 @@ def run_config(args):
 
     k, nq = 100, w.n_query
     out = {"workload": w.name, "n_base": w.n_base, "T": w.T, "M": w.M, "n_query": nq, "k": k, "dtype": "f32",
-           "data": "synthetic", "l2": "flushed between timed runs (512 MB write)", "timing": "median of 5 after 3 warm-up"}
-    if args.workload == "c3":
+           "data": "synthetic", "l2": "flushed between timed runs (512 MB write)",
+           "timing": "CUDA events, median of 5 after 3 warm-up (1 after 1 for the O(D) scorers)"}
+    nn = exact_nn_gpu(q[:1000], w, mix, dev)
+    if name == "c3":
         L, S = 30_000, 1000
         ix, out["build_s"] = build("global")
+        del learn
         ms32 = timed(lambda: ix.search(q, L, k, "fbpq"))
         a_ids, a_d = ix.search(q, L, k, "fbpq")
         A = a_ids.cpu().numpy()
-        nn = exact_nn_gpu(q[:1000], w, mix, dev)
         out.update({"L": L, "shortlist": S,
                     "lut": "int8 (per-query step) and fp16 (power-of-two step), offsets per sub-quantizer",
                     "fbpq_f32": {"qps": nq / (ms32 / 1e3), "ms": ms32, "recall": recall_of(a_ids[:1000], nn)}})
@@ -608,31 +624,51 @@ def run_config(args):
             out[key] = {"qps": nq / (ms / 1e3), "ms": ms, "recall": recall_of(b_ids[:1000], nn),
                         "identical_lists": float(same.all(1).float().mean()), "mean_top100_overlap": float(overlap),
                         "max_abs_dist_diff_same_rank": float((a_d - b_d).abs()[same].max()) if same.any() else None}
-    elif args.workload == "c4":
+        out["index"] = {"device_bytes": int(ix.info().device_bytes)}
+    elif name == "c4":
         Ls = np.round(10.0 ** np.random.default_rng(7).uniform(3.0, 5.0, nq)).astype(np.int64)
         out.update({"L": "round(10^U(3,5)) per query, seed 7", "L_mean": float(Ls.mean())})
-        nn = exact_nn_gpu(q[:1000], w, mix, dev)
         ixl, out["build_local_s"] = build("local")
         for scorer in ("hbpq", "hbpq_recon"):
-            ms = timed(lambda: ixl.search(q, Ls, k, scorer), reps=5 if scorer == "hbpq" else 1,
-                       warm=3 if scorer == "hbpq" else 1)
+            full = scorer == "hbpq"
+            ms = timed(lambda: ixl.search(q, Ls, k, scorer), reps=5 if full else 1, warm=3 if full else 1)
             ids, _ = ixl.search(q, Ls, k, scorer)
             out[scorer] = {"qps": nq / (ms / 1e3), "ms": ms, "recall": recall_of(ids[:1000], nn)}
+        out["index_local"] = {"device_bytes": int(ixl.info().device_bytes)}
         del ixl
         ixg, out["build_global_s"] = build("global")
+        del learn
         for scorer in ("fbpq", "recon"):
-            ms = timed(lambda: ixg.search(q, Ls, k, scorer))
+            full = scorer == "fbpq"
+            ms = timed(lambda: ixg.search(q, Ls, k, scorer), reps=5 if full else 1, warm=3 if full else 1)
             ids, _ = ixg.search(q, Ls, k, scorer)
             out[scorer] = {"qps": nq / (ms / 1e3), "ms": ms, "recall": recall_of(ids[:1000], nn)}
+        out["hbpq_over_fbpq_time"] = out["hbpq"]["ms"] / out["fbpq"]["ms"]
+        out["index_global"] = {"device_bytes": int(ixg.info().device_bytes)}
     else:
         ix, out["build_s"] = build("global")
+        del learn
+        info = ix.info()
+        cross_bytes = info.n_points * 4
+        out["index"] = {"device_bytes": int(info.device_bytes), "n_points": int(info.n_points),
+                        "per_point_cross_bytes": int(cross_bytes),
+                        "device_bytes_without_per_point_cross": int(info.device_bytes - cross_bytes)}
         out["batch"] = {}
         for L in w.L:
-            ms = timed(lambda: ix.search(q, L, k, "fbpq"))
-            out["batch"][f"L{L}"] = {"qps": nq / (ms / 1e3), "ms": ms}
-        out["serve"] = serve_block(ix, w, mix, k, args.serve_seconds)
-    out["index"] = {"device_bytes": int(ix.info().device_bytes) if args.workload != "c4" else int(ixg.info().device_bytes)}
-    print(json.dumps(out), flush=True)
+            for scorer in ("fbpq", "fbpq_tables"):
+                ms = timed(lambda: ix.search(q, L, k, scorer), reps=3, warm=2)
+                out["batch"][f"{scorer}_L{L}"] = {"qps": nq / (ms / 1e3), "ms": ms}
+        ids, _ = ix.search(q[:1000], 10_000, k, "fbpq")
+        out["recall_L10000"] = recall_of(ids, nn)
+        out["serve"] = serve_block(ix, w, mix, k, serve_seconds, n_max=200_000)
+    return out
+
+
+def run_config(args):
+    """--workload c3 | c4 | c5: one configuration block as its own JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(config_block(args.workload, args.serve_seconds)), flush=True)
 
 
 def recall(ix, queries, w, mix, L, k, dev, n_gt=1000):
