@@ -674,6 +674,30 @@ def recall_at(result_ids, nn_ids, R):
 
 
 # ----------------------------------------------------------------------------
+# Encoding error (§4.2, Fig. errors)
+# ----------------------------------------------------------------------------
+
+
+def encoding_error(cb: Codebooks, X, variant="global"):
+    """Squared encoding error ||x - xhat||^2 of every point (§4.2, Fig. errors: the
+    average of this over a dataset, with global codebooks (Eq. 7) or with the HBPQ
+    local codebooks (§3.2)).  The point is encoded as the index encodes it
+    (encode_multi_d_adc / encode_hbpq) and reconstructed from that code.
+    Returns FP64 (n,); exact integers on the integer grid."""
+    X = np.asarray(X, dtype=np.int64)
+    if variant == "global":
+        cells, codes = encode_multi_d_adc(X, cb)
+        xhat = reconstruct(cb, cells, codes)
+    elif variant == "local":
+        cells, codes = encode_hbpq(X, cb)
+        xhat = reconstruct_hbpq(cb, cells, codes)
+    else:
+        raise ValueError(variant)
+    diff = X.astype(np.float64) - xhat
+    return (diff * diff).sum(1)
+
+
+# ----------------------------------------------------------------------------
 # Memory accounting (§3.3)
 # ----------------------------------------------------------------------------
 

@@ -102,3 +102,33 @@ def test_train_shapes_and_local_training_improves_distortion():
     xg = O.reconstruct(cb, *O.encode_multi_d_adc(learn, cb))
     xl = O.reconstruct_hbpq(cbl, *O.encode_hbpq(learn, cbl))
     assert ((learn - xl) ** 2).sum() <= ((learn - xg) ** 2).sum()
+
+
+def test_encoding_error_literal():
+    """Fig. errors' quantity by hand (literal codebooks: C^1 = [[1, 2], [3, 4]],
+    C^2 = [[5, 6], [7, 8]], R_0[t] = (t, -t), R_1[t] = (2t, 1)).  x = (4, 4, 6, 5):
+    first half: 13 to c^1_0, 1 to c^1_1 -> i = 1; second half: 2 to c^2_0, 10 to
+    c^2_1 -> j = 0; displacement (1, 0 | 1, -1).  R_0: (t - 1)^2 + t^2 is 1 at t = 0
+    and t = 1 -> the lower index 0, error 1; R_1: (2t - 1)^2 + 4 is 5 at t = 0 and
+    t = 1 -> 0, error 5.  Total 6, cell 2, code (0, 0)."""
+    cb = literal_codebooks()
+    x = np.array([[4, 4, 6, 5]])
+    cells, codes = O.encode_multi_d_adc(x, cb)
+    assert cells.tolist() == [2] and codes.tolist() == [[0, 0]]
+    assert O.encoding_error(cb, x).tolist() == [6.0]
+
+
+def test_encoding_error_local_not_above_global_and_zero_case():
+    """Local codebooks started from the global ones never encode worse (Lloyd does not
+    raise distortion on their learn sets, which here are the encoded points), and a
+    codebook holding every displacement encodes with zero error."""
+    rng = np.random.default_rng(21)
+    learn = rng.integers(0, 256, size=(3000, 8)) // np.array([1, 1, 4, 4, 1, 1, 4, 4])
+    cb = O.train_multi_d_adc(learn, T=4, M=4, iters=3)
+    cbl = O.train_hbpq_local(learn, cb, iters=3)
+    eg = O.encoding_error(cb, learn, "global")
+    el = O.encoding_error(cbl, learn, "local")
+    assert el.sum() <= eg.sum() and el.sum() < eg.sum()
+    from test_oracle_scoring import zero_quantization_case
+    X, cbz = zero_quantization_case(0)
+    assert (O.encoding_error(cbz, X) == 0).all()
