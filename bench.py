@@ -600,6 +600,15 @@ def config_block(name, serve_seconds=0.25):
                 ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
 
+    def enc_error(ix, n=10_000_000):
+        """Mean squared encoding error ||x - xhat||^2 over the first n base points (§4.2, Fig. errors)."""
+        tot, cnt = 0.0, 0
+        for s0 in range(0, n, 2_000_000):
+            x = sdev.points_cuda(mix, sd.STREAM_BASE, s0, min(2_000_000, n - s0), device=dev)
+            tot += float(ix.encoding_error(x).double().sum())
+            cnt += x.shape[0]
+        return tot / cnt
+
     k, nq = 100, w.n_query
     out = {"workload": w.name, "n_base": w.n_base, "T": w.T, "M": w.M, "n_query": nq, "k": k, "dtype": "f32",
            "data": "synthetic", "l2": "flushed between timed runs (512 MB write)",
@@ -608,7 +617,12 @@ def config_block(name, serve_seconds=0.25):
     if name == "c3":
         L, S = 30_000, 1000
         ix, out["build_s"] = build("global")
+        loc16 = bpq.Index.train(learn, w.T, w.M, variant="local", iters=w.kmeans_iters)
         del learn
+        eg, el = enc_error(ix), enc_error(loc16)
+        del loc16
+        out["encoding_error_16B"] = {"global": eg, "local": el, "reduction": 1.0 - el / eg,
+                                     "points": "first 10M base points", "paper": "about 30 % lower (Fig. errors)"}
         ms32 = timed(lambda: ix.search(q, L, k, "fbpq"))
         a_ids, a_d = ix.search(q, L, k, "fbpq")
         A = a_ids.cpu().numpy()
@@ -629,6 +643,7 @@ def config_block(name, serve_seconds=0.25):
         Ls = np.round(10.0 ** np.random.default_rng(7).uniform(3.0, 5.0, nq)).astype(np.int64)
         out.update({"L": "round(10^U(3,5)) per query, seed 7", "L_mean": float(Ls.mean())})
         ixl, out["build_local_s"] = build("local")
+        el = enc_error(ixl)
         for scorer in ("hbpq", "hbpq_recon"):
             full = scorer == "hbpq"
             ms = timed(lambda: ixl.search(q, Ls, k, scorer), reps=5 if full else 1, warm=3 if full else 1)
@@ -638,6 +653,9 @@ def config_block(name, serve_seconds=0.25):
         del ixl
         ixg, out["build_global_s"] = build("global")
         del learn
+        eg = enc_error(ixg)
+        out["encoding_error_8B"] = {"global": eg, "local": el, "reduction": 1.0 - el / eg,
+                                    "points": "first 10M base points", "paper": "about 30 % lower (Fig. errors)"}
         for scorer in ("fbpq", "recon"):
             full = scorer == "fbpq"
             ms = timed(lambda: ixg.search(q, Ls, k, scorer), reps=5 if full else 1, warm=3 if full else 1)

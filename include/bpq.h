@@ -162,6 +162,17 @@ int bpq_encode(const bpq_index* idx, const float* x_dev, int64_t n, int32_t* cel
                uint8_t* codes_out_dev, void* stream);
 
 /*
+ * bpq_reconstruction_error — squared encoding error ||x - xhat||^2 of n points
+ * (§4.2, Fig. errors), xhat being the reconstruction of Eq. 7 (global variant)
+ * or of §3.2 (local codebooks of the cell's half-cells) from the given cell and
+ * code.  x_dev: n x D float32; cells_dev, codes_dev: as bpq_encode writes them
+ * (cell ids in [0, T*T), codes M bytes per point); err_dev: n float32.  The
+ * average over a dataset is the paper's average encoding error.
+ */
+int bpq_reconstruction_error(const bpq_index* idx, const float* x_dev, int64_t n, const int32_t* cells_dev,
+                             const uint8_t* codes_dev, float* err_dev, void* stream);
+
+/*
  * bpq_add — encode n points and append them to the pending set.  ids_dev: n
  * int32 >= 0 (NULL = consecutive ids starting at the number of points added so
  * far).  The points become searchable after bpq_finalize.  Total points < 2^32.

@@ -65,6 +65,7 @@ _SIGS = {
                                       ctypes.c_char_p, ctypes.c_int, _P]),
     "bpq_encode": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     "bpq_add": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    "bpq_reconstruction_error": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P]),
     "bpq_finalize": (ctypes.c_int, [_P, _P]),
     "bpq_query_tables": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P]),
     "bpq_search_workspace_size": (ctypes.c_size_t, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
@@ -227,6 +228,16 @@ class Index:
 
     def add(self, x, ids=None, stream=None):
         _check(lib().bpq_add(self._h, _ptr(x), x.shape[0], _ptr(ids), _stream(stream)))
+
+    def encoding_error(self, x, stream=None):
+        """Squared encoding error ||x - xhat||^2 of every row of x (bpq_encode, then
+        bpq_reconstruction_error): float32 (n,)."""
+        import torch
+        cells, codes = self.encode(x, stream)
+        err = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        _check(lib().bpq_reconstruction_error(self._h, _ptr(x), x.shape[0], _ptr(cells), _ptr(codes), _ptr(err),
+                                              _stream(stream)))
+        return err
 
     def finalize(self, stream=None):
         _check(lib().bpq_finalize(self._h, _stream(stream)))

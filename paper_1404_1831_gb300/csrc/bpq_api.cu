@@ -645,6 +645,19 @@ int bpq_encode(const bpq_index* ix, const float* x_dev, int64_t n, int32_t* cell
   });
 }
 
+int bpq_reconstruction_error(const bpq_index* ix, const float* x_dev, int64_t n, const int32_t* cells_dev,
+                             const uint8_t* codes_dev, float* err_dev, void* stream) {
+  return guard([&] {
+    BPQ_CHECK(ix, BPQ_EINVAL, "index is NULL");
+    BPQ_CHECK(n >= 0, BPQ_EINVAL, "n < 0");
+    if (n == 0) return;
+    BPQ_CHECK(n < ((int64_t)1 << 26) * 8, BPQ_EINVAL, "too many points in one call");
+    BPQ_CHECK(x_dev && cells_dev && codes_dev && err_dev, BPQ_EINVAL, "NULL pointer");
+    DeviceGuard dg(ix->device);
+    launch_reconstruction_error(*ix, x_dev, n, cells_dev, codes_dev, err_dev, static_cast<cudaStream_t>(stream));
+  });
+}
+
 int bpq_add(bpq_index* ix, const float* x_dev, int64_t n, const int32_t* ids_dev, void* stream) {
   return guard([&] {
     BPQ_CHECK(ix, BPQ_EINVAL, "index is NULL");

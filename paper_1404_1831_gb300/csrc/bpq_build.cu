@@ -149,6 +149,38 @@ __global__ void encode_kernel(const float* __restrict__ X, int64_t n, const floa
   }
 }
 
+// Squared encoding error ||x - xhat||^2 of n points from their cell and code
+// (§4.2, Fig. errors): xhat = [c^1_i; c^2_j] + the codewords of the code, from the
+// global codebooks R_k (Eq. 7) or the local codebooks Q^i_k, S^j_k (§3.2).  One
+// warp per point, lanes over the dimensions (coalesced rows of x).
+__global__ void recon_error_kernel(const float* __restrict__ X, int64_t n, const int32_t* __restrict__ cells,
+                                   const uint8_t* __restrict__ codes, const float* __restrict__ C1,
+                                   const float* __restrict__ C2, int T, int D, int M, const float* __restrict__ R,
+                                   const float* __restrict__ Q, const float* __restrict__ S, float* __restrict__ err) {
+  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (p >= n) return;  // uniform over the warp
+  const int H = D / 2, s = D / M, m2 = M / 2;
+  const int cell = cells[p];
+  const int i = cell / T, j = cell - i * T;
+  float acc = 0.f;
+  for (int d = lane; d < D; d += 32) {
+    const int k = d / s, t = d - k * s;
+    const int c = codes[p * M + k];
+    const bool second = d >= H;
+    const float cen = second ? C2[(int64_t)j * H + d - H] : C1[(int64_t)i * H + d];
+    float r;
+    if (Q)
+      r = second ? S[(((int64_t)j * m2 + k - m2) * KSUB + c) * s + t] : Q[(((int64_t)i * m2 + k) * KSUB + c) * s + t];
+    else
+      r = R[((int64_t)k * KSUB + c) * s + t];
+    const float e = X[p * D + d] - (cen + r);
+    acc = fmaf(e, e, acc);
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) err[p] = acc;
+}
+
 __global__ void seq_ids_kernel(int32_t* ids, int64_t n, int64_t start) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p < n) ids[p] = (int32_t)(start + p);
@@ -442,6 +474,17 @@ void launch_encode(const bpq_index& ix, const float* x, int64_t n, int32_t* cell
   else if (D == 32 && M == 8) encode_t<16, 4>(ix, x, n, cell, codes, st);
   else if (D == 8 && M == 8) encode_t<4, 1>(ix, x, n, cell, codes, st);
   else throw Error(BPQ_EINVAL, "unsupported (D, M) for encoding");
+}
+
+void launch_reconstruction_error(const bpq_index& ix, const float* x, int64_t n, const int32_t* cells,
+                                 const uint8_t* codes, float* err, cudaStream_t st) {
+  if (n <= 0) return;
+  const bool local = ix.p.variant == BPQ_VARIANT_LOCAL;
+  const int64_t threads = n * 32;
+  recon_error_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+      x, n, cells, codes, ix.C1.as<float>(), ix.C2.as<float>(), ix.p.T, ix.p.D, ix.p.M, ix.R.as<float>(),
+      local ? ix.Q.as<float>() : nullptr, local ? ix.S.as<float>() : nullptr, err);
+  check_launch("reconstruction error kernel");
 }
 
 void fill_sequential_ids(int32_t* ids, int64_t n, int64_t start, cudaStream_t st) {

@@ -367,6 +367,8 @@ void launch_encode(const bpq_index& ix, const float* x, int64_t n, int32_t* cell
 void finalize_lists(bpq_index& ix, cudaStream_t st);
 void train_codebooks(bpq_index& ix, const float* learn, int64_t n, cudaStream_t st);
 void fill_sequential_ids(int32_t* ids, int64_t n, int64_t start, cudaStream_t st);
+void launch_reconstruction_error(const bpq_index& ix, const float* x, int64_t n, const int32_t* cells,
+                                 const uint8_t* codes, float* err, cudaStream_t st);
 void build_point_cross(bpq_index& ix, cudaStream_t st);  // per-point Eq. 9 cross terms
 
 }  // namespace bpq

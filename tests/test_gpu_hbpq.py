@@ -113,3 +113,19 @@ def test_hbpq_chunked_workspace(hbpq, tiny_oracle):
     ids, d = ix.search(q, 4000, 50, "hbpq", workspace=ws)
     o_ids, o_d, _ = O.search(hbpq["oix"], qn, 4000, 50, "hbpq")
     assert assert_topk_match(ids.cpu().numpy(), d.cpu().numpy(), o_ids, o_d) == len(qn)
+
+
+def test_encoding_error_matches_oracle(hbpq, tiny_oracle):
+    """Fig. errors' per-point squared encoding error on the GPU equals the oracle's,
+    bit for bit (integer grid), for the local codebooks and the global ones.  (Which
+    is lower depends on the data: with 20k learn points over 64 half-cells the local
+    codebooks have about 300 points for 256 codewords and do not generalize.)"""
+    import paper_1404_1831_gb300 as bpq
+    X = tiny_oracle["base"][:20_000]
+    x = torch.as_tensor(X, dtype=torch.float32, device=DEV)
+    got = hbpq["ix"].encoding_error(x).cpu().numpy()
+    assert np.array_equal(got.astype(np.float64), O.encoding_error(hbpq["cbl"], X, "local"))
+    cb = O.train_multi_d_adc(tiny_oracle["learn"], hbpq["cbl"].T, hbpq["cbl"].M, 4)
+    g = bpq.Index.create(cb.C1, cb.C2, cb.R)
+    got_g = g.encoding_error(x).cpu().numpy()
+    assert np.array_equal(got_g.astype(np.float64), O.encoding_error(cb, X, "global"))
