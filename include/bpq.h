@@ -412,6 +412,58 @@ int bpq_server_get_stats(const bpq_server* s, bpq_server_stats* out);
 /* bpq_server_free — waits for the slots' streams and releases the server (NULL is allowed). */
 void bpq_server_free(bpq_server* s);
 
+/*
+ * bpq_set_scan_work_size — how bpq_search schedules the scan of the FBPQ and
+ * HBPQ scorers (k <= 128).  0 (the default): one CTA per query.  W > 0: the
+ * visited cells of each query are cut into contiguous work items of about W
+ * candidates (at most 16 items per query), a persistent wave of CTAs takes the
+ * items from a queue, and the partial top-k lists of a split query are merged by
+ * (distance, id); the answers are the same.  Long queries then no longer set the
+ * batch's tail.  bpq_autotune picks W by measurement.  Errors: BPQ_EINVAL.
+ */
+int bpq_set_scan_work_size(bpq_index* idx, int32_t candidates_per_item);
+
+/*
+ * bpq_autotune — picks the scan schedule of bpq_search for one batch class by
+ * measurement: runs the batch (queries_dev, nq, budgets, k, scorer and outputs as
+ * for bpq_search; the call allocates a workspace for the whole batch) with each
+ * candidate work-item size W in {0, 4096, 8192, 16384, 32768} (0: one CTA per
+ * query; W: the persistent work-queue scan of bpq_set_scan_work_size), four
+ * timed runs each with CUDA events on `stream` (the first discarded), and keeps the
+ * fastest for the class (scorer, k <= 32, floor(log2 nq), floor(log2 mean L)).
+ * Later bpq_search calls of that class use it; other classes keep the index's
+ * setting.  chosen_out (may be NULL) receives the chosen W.  Synchronizes the
+ * stream.  The outputs hold the last run's (identical) answers.  (An engineering
+ * step of this library; the paper has no scheduling.)
+ */
+int bpq_autotune(bpq_index* idx, const float* queries_dev, int64_t nq, const int64_t* L_host, int64_t L_stride,
+                 int32_t k, int32_t scorer, int32_t* ids_dev, float* dists_dev, void* stream, int32_t* chosen_out);
+
+/*
+ * Search graphs: one batch shape of bpq_search captured as a CUDA graph and
+ * replayed with one launch (every kernel, memset and budget copy of the
+ * pipeline), for repeated batches of the same shape where per-kernel launch costs
+ * matter.  bpq_graph_create captures the search of nq queries read from
+ * queries_dev with results written to ids_dev / dists_dev (nq x k, as
+ * bpq_search): those device buffers are fixed for the graph's lifetime (write new
+ * queries into queries_dev before a launch).  The graph owns a workspace for the
+ * whole batch and page-locked budgets: L_host / L_stride as bpq_search; with
+ * per-query budgets (L_stride == 1), bpq_graph_set_budgets replaces them (values
+ * in [1, the largest budget given at creation]), read by the next launches (do not
+ * call it while a launch of the graph is in flight).  The scan schedule in force
+ * at creation (bpq_set_scan_work_size, or a bpq_autotune choice for the class) is
+ * captured.  bpq_graph_create runs the search once uncaptured and synchronizes;
+ * bpq_graph_launch is asynchronous on `stream`.  The index must stay unchanged
+ * while the graph exists.  Errors: BPQ_EINVAL, BPQ_ESTATE, BPQ_ENOMEM, BPQ_ECUDA.
+ */
+typedef struct bpq_graph bpq_graph;
+int bpq_graph_create(bpq_graph** out, const bpq_index* idx, const float* queries_dev, int64_t nq,
+                     const int64_t* L_host, int64_t L_stride, int32_t k, int32_t scorer, int32_t* ids_dev,
+                     float* dists_dev);
+int bpq_graph_set_budgets(bpq_graph* g, const int64_t* L_host);
+int bpq_graph_launch(bpq_graph* g, void* stream);
+void bpq_graph_free(bpq_graph* g);
+
 /* bpq_info / bpq_arrays — sizes and read-only device views (see the structs). */
 int bpq_get_info(const bpq_index* idx, bpq_info* out);
 int bpq_get_arrays(const bpq_index* idx, bpq_arrays* out);

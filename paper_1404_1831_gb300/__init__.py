@@ -76,6 +76,14 @@ _SIGS = {
                                   _P, _P, ctypes.c_size_t, _P]),
     "bpq_search_status": (ctypes.c_int, [_P, _P, _P]),
     "bpq_set_hbpq_table_budget": (ctypes.c_int, [_P, ctypes.c_double]),
+    "bpq_set_scan_work_size": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "bpq_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P,
+                                    _P, _P, _P]),
+    "bpq_graph_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, _P, ctypes.c_int64, _P, ctypes.c_int64,
+                                        ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "bpq_graph_set_budgets": (ctypes.c_int, [_P, _P]),
+    "bpq_graph_launch": (ctypes.c_int, [_P, _P]),
+    "bpq_graph_free": (None, [_P]),
     "bpq_search_shortlist_workspace_size": (ctypes.c_size_t, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32]),
     "bpq_search_shortlist": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_size_t, _P]),
@@ -374,6 +382,26 @@ class Index:
         """Table slots reserved per query by the HBPQ table form (0 = automatic)."""
         _check(lib().bpq_set_hbpq_table_budget(self._h, float(slots_per_query)))
 
+    def set_scan_work_size(self, candidates_per_item):
+        """0: one CTA per query; W > 0: persistent work-queue scan with items of about W candidates."""
+        _check(lib().bpq_set_scan_work_size(self._h, int(candidates_per_item)))
+
+    def autotune(self, q, L, k, scorer="fbpq", stream=None):
+        """bpq_autotune on this batch: returns the chosen work-item size (0 = one CTA per query)."""
+        import torch
+        nq = q.shape[0]
+        Ls, stride = _L_array(L, nq)
+        ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=q.device)
+        chosen = ctypes.c_int32()
+        _check(lib().bpq_autotune(self._h, _ptr(q), nq, Ls.ctypes.data, stride, k, SCORERS[scorer], _ptr(ids),
+                                  _ptr(dists), _stream(stream), ctypes.byref(chosen)))
+        return chosen.value
+
+    def graph(self, q, L, k, scorer="fbpq"):
+        """A SearchGraph: this batch shape captured once, replayed by launch()."""
+        return SearchGraph(self, q, L, k, scorer)
+
     def search_status(self, workspace=None, stream=None):
         ws = workspace if workspace is not None else self._ws
         _check(lib().bpq_search_status(self._h, _ptr(ws), _stream(stream)))
@@ -388,6 +416,43 @@ class Index:
         _check(lib().bpq_search_host(self._h, q.ctypes.data, nq, Ls.ctypes.data, stride, k, SCORERS[scorer],
                                      ids.ctypes.data, dists.ctypes.data, _stream(stream)))
         return ids, dists
+
+
+class SearchGraph:
+    """bpq_graph_*: static device buffers q (nq, D), ids / dists (nq, k); write new
+    queries into .q (and new budgets with set_budgets) before launch()."""
+
+    def __init__(self, index, q, L, k, scorer="fbpq"):
+        import torch
+        self.index = index
+        self.q = q
+        nq = q.shape[0]
+        self.ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+        self.dists = torch.empty((nq, k), dtype=torch.float32, device=q.device)
+        Ls, stride = _L_array(L, nq)
+        h = ctypes.c_void_p()
+        _check(lib().bpq_graph_create(ctypes.byref(h), index._h, _ptr(q), nq, Ls.ctypes.data, stride, k,
+                                      SCORERS[scorer], _ptr(self.ids), _ptr(self.dists)))
+        self._h = h
+
+    def set_budgets(self, L):
+        Ls = np.ascontiguousarray(L, dtype=np.int64)
+        _check(lib().bpq_graph_set_budgets(self._h, Ls.ctypes.data))
+
+    def launch(self, stream=None):
+        _check(lib().bpq_graph_launch(self._h, _stream(stream)))
+        return self.ids, self.dists
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().bpq_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def header_symbols():

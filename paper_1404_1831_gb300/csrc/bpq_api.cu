@@ -2,6 +2,7 @@
 // workspace layout and the query pipeline
 //   tables (K1/K2) -> traversal (K4) -> scan + top-k (K5/K6)
 // enqueued on the caller's stream, chunk by chunk when the workspace is small.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -113,13 +114,22 @@ int64_t hbpq_slot_limit(const bpq_index& ix) { return (((int64_t)1 << 32) - 1) /
 struct Layout {
   size_t status, qcounter, L, d1, d2, lut, cells, ncells, npoints, total;
   size_t hb_qbase, hb_qrows, hb_qbits, hb_hmap, hb_ctr, hb_fb, hb_tab;
+  size_t wq_ctr, wq_items, wq_merges, wq_pids, wq_pdists;  // work-queue scan
   int64_t cap, hb_slots;
+  bool wq;
 };
+
+// The persistent work-queue form of the segment scans (FBPQ per-point and the
+// HBPQ table form, k <= 128) when a work-item size W > 0 is in force.
+bool work_queue_used(int W, int scorer, int k) {
+  return W > 0 && k <= 128 && (scorer == BPQ_SCORER_FBPQ || scorer == BPQ_SCORER_HBPQ);
+}
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 Layout layout(const bpq_index& ix, int64_t nq, int64_t L_max, int scorer, bool with_cells, int k = 1,
-              double hb_per_query = 0.0) {
+              double hb_per_query = 0.0, int work_W = -1) {
+  if (work_W < 0) work_W = ix.scan_work_W;
   Layout l{};
   size_t o = 0;
   l.status = o;
@@ -159,6 +169,20 @@ Layout layout(const bpq_index& ix, int64_t nq, int64_t L_max, int scorer, bool w
     o = align_up(o + (size_t)nq * 4);
     l.hb_tab = o;
     o = align_up(o + (size_t)l.hb_slots * ix.m2 * KSUB * 4);
+  }
+  l.wq = with_cells && work_queue_used(work_W, scorer, k);
+  if (l.wq) {
+    const size_t parts = (size_t)nq * SCAN_MAX_ITEMS;
+    l.wq_ctr = o;
+    o = align_up(o + 16);
+    l.wq_items = o;
+    o = align_up(o + parts * 16);
+    l.wq_merges = o;
+    o = align_up(o + (size_t)nq * 16);
+    l.wq_pids = o;
+    o = align_up(o + parts * k * 4);
+    l.wq_pdists = o;
+    o = align_up(o + parts * k * 4);
   }
   l.total = o;
   return l;
@@ -261,7 +285,19 @@ void bpq::run_queries(const bpq_index& ix, const float* q, int64_t nq, const int
       hb_per_query = hbpq_slots_per_query(ix, (double)L_max);
     }
   }
-  auto lay = [&](int64_t n) { return layout(ix, n, L_max, scorer, scan, k, hb_per_query); };
+  // work-item size: the autotuner's choice for this batch class, else the index's setting
+  int work_W = ix.scan_work_W;
+  if (scan && !ix.tuned_W.empty()) {
+    double Lm = (double)L_max;
+    if (L_stride) {
+      Lm = 0.0;
+      for (int32_t v : Lq) Lm += v;
+      Lm /= (double)nq;
+    }
+    const auto it = ix.tuned_W.find(tune_key(scorer, k, nq, Lm));
+    if (it != ix.tuned_W.end()) work_W = it->second;
+  }
+  auto lay = [&](int64_t n) { return layout(ix, n, L_max, scorer, scan, k, hb_per_query, work_W); };
   // largest chunk that fits the workspace (and, for HBPQ, whose table offsets fit 32 bits)
   auto fits = [&](int64_t n) {
     return lay(n).total <= ws_bytes && !(hb && hb_per_query * (double)n > (double)hbpq_slot_limit(ix));
@@ -349,6 +385,18 @@ void bpq::run_queries(const bpq_index& ix, const float* q, int64_t nq, const int
       sa.hb_tables = h.tables;
       sa.qlist = h.fallback;
       sa.qlist_n = h.fb_count;
+    }
+    if (l.wq) {
+      sa.work_W = work_W;
+      int32_t* ctr = reinterpret_cast<int32_t*>(w + l.wq_ctr);
+      sa.n_items = ctr;
+      sa.item_counter = ctr + 1;
+      sa.part_counter = ctr + 2;
+      sa.n_merges = ctr + 3;
+      sa.items = reinterpret_cast<int4*>(w + l.wq_items);
+      sa.merges = reinterpret_cast<int4*>(w + l.wq_merges);
+      sa.part_ids = reinterpret_cast<int32_t*>(w + l.wq_pids);
+      sa.part_dists = reinterpret_cast<float*>(w + l.wq_pdists);
     }
     launch_scan(sa, scorer, st);
   }
@@ -567,6 +615,12 @@ bpq_index* load_file(const char* path, int device) {
 
 void bpq::set_last_error(const std::string& msg) { g_last_error = msg; }
 
+uint64_t bpq::tune_key(int scorer, int k, int64_t nq, double L_mean) {
+  const uint64_t lq = (uint64_t)std::floor(std::log2((double)std::max<int64_t>(nq, 1)));
+  const uint64_t lL = (uint64_t)std::floor(std::log2(std::max(1.0, L_mean)));
+  return ((uint64_t)scorer << 24) | ((uint64_t)(k <= 32) << 20) | (lq << 8) | lL;
+}
+
 extern "C" {
 
 const char* bpq_last_error(void) { return g_last_error.c_str(); }
@@ -730,7 +784,10 @@ int bpq_query_tables(const bpq_index* ix, const float* q, int64_t nq, float* d1,
 
 size_t bpq_search_workspace_size(const bpq_index* ix, int64_t nq, int64_t L_max, int32_t k, int32_t scorer) {
   if (!ix || nq < 0 || L_max < 1) return 0;
-  return layout(*ix, std::max<int64_t>(nq, 1), L_max, scorer, true, k).total;
+  // room for the work-queue form whenever the index may use it (its setting or a tuned class)
+  int W = ix->scan_work_W;
+  for (const auto& e : ix->tuned_W) W = std::max(W, e.second);
+  return layout(*ix, std::max<int64_t>(nq, 1), L_max, scorer, true, k, 0.0, W).total;
 }
 
 int bpq_traverse(const bpq_index* ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride,
@@ -839,6 +896,82 @@ int bpq_set_hbpq_table_budget(bpq_index* ix, double slots_per_query) {
     BPQ_CHECK(std::isfinite(slots_per_query) && slots_per_query >= 0.0, BPQ_EINVAL,
               "slots per query must be finite and >= 0");
     ix->hb_slots_per_query = slots_per_query;
+  });
+}
+
+int bpq_autotune(bpq_index* ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride, int32_t k,
+                 int32_t scorer, int32_t* ids, float* dists, void* stream, int32_t* chosen_out) {
+  return guard([&] {
+    check_searchable(ix);
+    BPQ_CHECK(nq >= 1 && q && ids && dists, BPQ_EINVAL, "bad argument");
+    BPQ_CHECK(k >= 1 && k <= MAX_K, BPQ_EINVAL, "k must be in [1, 1024]");
+    check_scorer(*ix, scorer);
+    DeviceGuard dg(ix->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<int32_t> Lq;
+    const int64_t L_max = read_L(L_host, L_stride, nq, &Lq);
+    double Lm = (double)L_max;
+    if (L_stride) {
+      Lm = 0.0;
+      for (int32_t v : Lq) Lm += v;
+      Lm /= (double)nq;
+    }
+    const uint64_t key = tune_key(scorer, k, nq, Lm);
+    ix->tuned_W.erase(key);
+    const int32_t cand[] = {0, 4096, 8192, 16384, 32768};
+    // one workspace that holds the batch in one chunk with either schedule
+    DevBuf wsb;
+    wsb.alloc(layout(*ix, nq, L_max, scorer, true, k, 0.0, work_queue_used(1, scorer, k) ? 1 : 0).total);
+    void* ws = wsb.p;
+    const size_t ws_bytes = wsb.bytes;
+    cudaEvent_t e0, e1;
+    BPQ_CUDA(cudaEventCreate(&e0));
+    BPQ_CUDA(cudaEventCreate(&e1));
+    int32_t best = 0;
+    float best_ms = 0.f;
+    const int32_t saved = ix->scan_work_W;
+    try {
+      for (int32_t W : cand) {
+        if (W > 0 && !work_queue_used(W, scorer, k)) continue;
+        if (layout(*ix, nq, L_max, scorer, true, k, 0.0, W).total > ws_bytes) continue;  // must run in one chunk
+        ix->scan_work_W = W;
+        std::vector<float> t;
+        for (int r = 0; r < 4; ++r) {  // the first run of a configuration is a warm-up
+          BPQ_CUDA(cudaEventRecord(e0, st));
+          run_queries(*ix, q, nq, L_host, L_stride, k, scorer, ids, dists, nullptr, 0, nullptr, nullptr, ws, ws_bytes,
+                      st);
+          BPQ_CUDA(cudaEventRecord(e1, st));
+          BPQ_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          BPQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (r > 0) t.push_back(ms);
+        }
+        std::sort(t.begin(), t.end());
+        const float med = t[t.size() / 2];
+        if (W == 0 || med < best_ms) {
+          best = W;
+          best_ms = med;
+        }
+      }
+    } catch (...) {
+      ix->scan_work_W = saved;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    ix->scan_work_W = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ix->tuned_W[key] = best;
+    if (chosen_out) *chosen_out = best;
+  });
+}
+
+int bpq_set_scan_work_size(bpq_index* ix, int32_t candidates_per_item) {
+  return guard([&] {
+    BPQ_CHECK(ix, BPQ_EINVAL, "index is NULL");
+    BPQ_CHECK(candidates_per_item >= 0, BPQ_EINVAL, "candidates per item must be >= 0");
+    ix->scan_work_W = candidates_per_item;
   });
 }
 

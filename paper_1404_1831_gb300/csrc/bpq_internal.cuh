@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <stdexcept>
 #include <string>
 
@@ -218,6 +219,10 @@ struct bpq_index {
   bpq::DevBuf Qb, Sb, E1, E2;
   bool local_bf16_exact = false;
   double hb_slots_per_query = 0.0;  // 0: automatic (bpq_set_hbpq_table_budget)
+  int32_t scan_work_W = 0;          // candidates per work item of the scan; 0: one CTA per query
+  // work-item sizes chosen by bpq_autotune, per batch class (scorer, k <= 32, log2 nq,
+  // log2 mean L); a class found here overrides scan_work_W
+  std::map<uint64_t, int32_t> tuned_W;
   int64_t n_points = 0, n_nonempty = 0, max_cell = 0;
   // workspace owned by bpq_search_host
   bpq::DevBuf host_ws, host_q, host_ids, host_dists;
@@ -325,7 +330,20 @@ struct ScanArgs {
   // reconstruction scans: when set, only the queries qlist[0 .. *qlist_n) are scored
   const int32_t* qlist;
   const int32_t* qlist_n;
+  // persistent work-queue scan (work_W > 0, segment scans only): items (q, first
+  // cell, end cell, partial slot or -1), counters (zeroed by the launcher), merge
+  // records (q, first slot, items) and the partial lists
+  int32_t work_W;
+  int4* items;
+  int32_t* n_items;
+  int32_t* item_counter;
+  int32_t* part_counter;
+  int4* merges;
+  int32_t* n_merges;
+  int32_t* part_ids;
+  float* part_dists;
 };
+constexpr int SCAN_MAX_ITEMS = 16;  // work items per query at most
 void launch_scan(const ScanArgs& a, int scorer, cudaStream_t st);
 // Shortlist scan with the int8 (f16 = false) or FP16 table: sl_out[q][0..k) =
 // the k best (score, position), EMPTY padded.
@@ -354,6 +372,9 @@ bool scan_supported(int D, int M);  // (D, M) shapes the scan kernels are built 
 
 // Text returned by bpq_last_error on the calling thread (bpq_api.cu).
 void set_last_error(const std::string& msg);
+
+// Batch class of the autotuner's table: scorer, k <= 32, floor(log2 nq), floor(log2 mean L).
+uint64_t tune_key(int scorer, int k, int64_t nq, double L_mean);
 
 // The search pipeline of bpq_search / bpq_traverse (bpq_api.cu).
 void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride,

@@ -746,14 +746,41 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
   __shared__ int cut_red[2 * NW];
   __shared__ int fcount;
   __shared__ unsigned long long thr;
+  __shared__ int64_t s_item;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int k = a.k;
   uint64_t* wb = wbuf + w * KW;
   uint32_t* hist = whist + w * 256;
   const char* lutb = reinterpret_cast<const char*>(lut);
 
-  for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
-    __syncthreads();  // the previous query's final list (in the table area) is written out
+  // One unit of work per iteration: a whole query (a.items == NULL, CTAs strided
+  // over the queries), or a work item (q, cells c_lo .. c_hi - 1, partial slot)
+  // taken from the queue (persistent CTAs); a split query's items write partial
+  // top-k lists that merge_parts_kernel combines.
+  for (int64_t iter = blockIdx.x;; iter += gridDim.x) {
+    __syncthreads();  // the previous unit's final list (in the table area) is written out
+    int64_t q, out_row;
+    int c_lo = 0, c_hi;
+    bool part = false;
+    if (a.items) {
+      if (threadIdx.x == 0) s_item = atomicAdd(a.item_counter, 1);
+      __syncthreads();
+      const int64_t it = s_item;
+      if (it >= *a.n_items) break;
+      const int4 itm = a.items[it];
+      q = itm.x;
+      c_lo = itm.y;
+      c_hi = itm.z;
+      part = itm.w >= 0;
+      out_row = part ? itm.w : q;
+    } else {
+      if (iter >= a.nq) break;
+      q = iter;
+      c_hi = max(0, a.ncells[q]);
+      out_row = q;
+    }
+    int32_t* o_ids = (part ? a.part_ids : a.out_ids) + out_row * k;
+    float* o_dists = (part ? a.part_dists : a.out_dists) + out_row * k;
     int hb_base = 0, hb_rows = 0, TW = 0;
     if constexpr (HB) {
       hb_base = a.hb_qbase[q];
@@ -775,10 +802,9 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
     }
     if (threadIdx.x == 0) thr = EMPTY;
     int wn = 0;  // entries in this warp's buffer (uniform across the warp)
-    const int nc = max(0, a.ncells[q]);
     const bpq_cell* cl = a.cells + q * (int64_t)a.cap;
-    for (int cs = 0; cs < nc; cs += CH) {
-      const int nch = min(CH, nc - cs);
+    for (int cs = c_lo; cs < c_hi; cs += CH) {
+      const int nch = min(CH, c_hi - cs);
       // first candidate of each cell of the chunk (thread t takes cells
       // tR .. tR + R - 1; the second read of a cell hits the cache)
       int loc = 0;
@@ -970,13 +996,104 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
       int r = 0;
       for (int j = 0; j < m; ++j) r += (wbuf[j] < x || (wbuf[j] == x && j < t)) ? 1 : 0;
       if (r < k) {
-        a.out_ids[q * k + r] = (int32_t)(uint32_t)x;
-        a.out_dists[q * k + r] = ord2f((uint32_t)(x >> 32));
+        o_ids[r] = (int32_t)(uint32_t)x;
+        o_dists[r] = ord2f((uint32_t)(x >> 32));
       }
     }
     for (int r = m + threadIdx.x; r < k; r += NT) {
-      a.out_ids[q * k + r] = -1;
-      a.out_dists[q * k + r] = __int_as_float(0x7f800000);
+      o_ids[r] = -1;
+      o_dists[r] = __int_as_float(0x7f800000);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Work items for the persistent scan: one warp per query cuts its visited cells
+// into contiguous ranges of about W candidates (cell c goes to range
+// floor(start_c / W'), start_c = the candidates before it, W' = max(W,
+// ceil(P / MAX_ITEMS)) for a query of P candidates), so that no unit of work is
+// much longer than W and the queue finishes evenly whatever the budgets.  A query
+// of one range writes its final list; a split query's ranges write partial
+// lists in consecutive slots and the query is listed for the merge.
+// ---------------------------------------------------------------------------
+constexpr int MAX_ITEMS = SCAN_MAX_ITEMS;
+
+__global__ void __launch_bounds__(128) build_items_kernel(ScanArgs a, int32_t W) {
+  __shared__ int bnd_s[4][MAX_ITEMS + 1];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * 4 + w;
+  if (q >= a.nq) return;  // uniform over the warp
+  if (a.hb_qbase && a.hb_qbase[q] < 0) return;  // scored by the HBPQ fallback
+  const int nc = max(0, a.ncells[q]);
+  const bpq_cell* cl = a.cells + q * (int64_t)a.cap;
+  long long P = 0;
+  for (int c = lane; c < nc; c += 32) P += cl[c].count;
+  P = warp_sum(P);
+  const long long Wq = max((long long)W, (P + MAX_ITEMS - 1) / MAX_ITEMS);
+  int* bnd = bnd_s[w];  // first cell of each range
+  int nb = 0;
+  long long run = 0;
+  int prev_j = -1;
+  for (int c0 = 0; c0 < nc; c0 += 32) {
+    const int c = c0 + lane;
+    const long long cnt = c < nc ? (long long)cl[c].count : 0;
+    long long incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const long long start = run + incl - cnt;
+    const int j = c < nc ? (int)(start / Wq) : -1;
+    const int jp = __shfl_up_sync(0xffffffffu, j, 1);
+    const bool first = c < nc && (lane == 0 ? j != prev_j : j != jp);
+    const unsigned m = __ballot_sync(0xffffffffu, first);
+    if (first) bnd[nb + __popc(m & lanemask_lt())] = c;
+    nb += __popc(m);
+    prev_j = __shfl_sync(0xffffffffu, j, 31);
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (nb == 0) bnd[nb++] = 0;  // a query without cells: one (empty) range pads its output
+  __syncwarp();
+  int base = 0, slot0 = -1;
+  if (lane == 0) {
+    base = atomicAdd(a.n_items, nb);
+    if (nb > 1) {
+      slot0 = atomicAdd(a.part_counter, nb);
+      a.merges[atomicAdd(a.n_merges, 1)] = make_int4((int)q, slot0, nb, 0);
+    }
+  }
+  base = __shfl_sync(0xffffffffu, base, 0);
+  slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+  for (int b = lane; b < nb; b += 32)
+    a.items[base + b] = make_int4((int)q, bnd[b], b + 1 < nb ? bnd[b + 1] : max(nc, 0), nb > 1 ? slot0 + b : -1);
+}
+
+// The k best (distance, id) of a split query's partial lists (all sorted, each
+// the exact k best of its range), ascending; equal entries (a point added twice
+// under one id) stay adjacent and both count.
+__global__ void __launch_bounds__(256) merge_parts_kernel(ScanArgs a) {
+  __shared__ uint64_t buf[MAX_ITEMS * 128];
+  for (int64_t r = blockIdx.x; r < *a.n_merges; r += gridDim.x) {
+    __syncthreads();
+    const int4 mg = a.merges[r];
+    const int q = mg.x, slot0 = mg.y, nb = mg.z, k = a.k;
+    const int n = nb * k;
+    int n2 = 64;
+    while (n2 < n) n2 <<= 1;
+    for (int e = threadIdx.x; e < n2; e += 256) {
+      uint64_t x = EMPTY;
+      if (e < n) {
+        const int32_t id = a.part_ids[(int64_t)slot0 * k + e];
+        if (id >= 0) x = ((uint64_t)f2ord(a.part_dists[(int64_t)slot0 * k + e]) << 32) | (uint32_t)id;
+      }
+      buf[e] = x;
+    }
+    block_bitonic_sort(buf, n2);
+    for (int e = threadIdx.x; e < k; e += 256) {
+      const uint64_t x = buf[e];
+      a.out_ids[(int64_t)q * k + e] = x == EMPTY ? -1 : (int32_t)(uint32_t)x;
+      a.out_dists[(int64_t)q * k + e] = x == EMPTY ? __int_as_float(0x7f800000) : ord2f((uint32_t)(x >> 32));
     }
   }
 }
@@ -1180,6 +1297,23 @@ void run_fbpq_seg(const ScanArgs& a, cudaStream_t st) {
   BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // HB reads its tables through L1: shared memory for five CTAs (132 KB), the rest as cache
   if (HB) BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 57));
+  if (a.work_W > 0) {
+    // persistent work-queue form: items, one resident wave of CTAs, merge of split queries
+    BPQ_CHECK(a.items && a.n_items && a.item_counter && a.part_counter && a.merges && a.n_merges && a.part_ids &&
+                  a.part_dists && a.k <= 128,
+              BPQ_EINVAL, "work-queue scan: missing buffers or k > 128");
+    BPQ_CUDA(cudaMemsetAsync(a.n_items, 0, 4 * sizeof(int32_t), st));  // n_items, item_counter, part_counter, n_merges
+    build_items_kernel<<<(unsigned)((a.nq + 3) / 4), 128, 0, st>>>(a, a.work_W);
+    check_launch("work item kernel");
+    int per_sm = 0;
+    BPQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+    const int grid = std::max(1, per_sm) * a.sm_count;
+    kern<<<grid, NT, smem, st>>>(a);
+    check_launch("fbpq segment scan kernel (work queue)");
+    merge_parts_kernel<<<(unsigned)std::min<int64_t>(a.nq, (int64_t)a.sm_count * 4), 256, 0, st>>>(a);
+    check_launch("partial list merge kernel");
+    return;
+  }
   const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
   kern<<<grid, NT, smem, st>>>(a);
   check_launch("fbpq segment scan kernel");
