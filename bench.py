@@ -435,6 +435,9 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_sweep:
         out["sweep"] = sweep(ix, queries, w, k, flush, stream)
         out["recall"] = recall(ix, queries, w, mix, L, k, dev)
+        out["batching"] = {"timing": "host wall time per batch over 50 back-to-back launches",
+                           "shapes": [batching_block(ix, queries[:nb].clone(), Lb, k, scorer)
+                                      for nb, Lb in ((16, 1_000), (64, 10_000), (64, 100_000), (512, 100_000))]}
     if rank == 0 and world == 1 and not args.no_serve:
         out["serve"] = serve_block(ix, w, mix, k, args.serve_seconds)
 
@@ -469,6 +472,7 @@ def serve_block(ix, w, mix, k, seconds, seed=11, n_max=300_000, max_batch=4096, 
     queued at time zero), next to the blocking queue (one bpq_search_host call at a time) at the same
     offered rates."""
     import numpy as np
+    import torch
 
     import synthdata as sd
     from paper_1404_1831_gb300 import serving
@@ -477,6 +481,10 @@ def serve_block(ix, w, mix, k, seconds, seed=11, n_max=300_000, max_batch=4096, 
     mix_L = np.array([1_000, 10_000, 100_000], dtype=np.int64)
     Ls = mix_L[np.random.default_rng(seed).integers(0, len(mix_L), n_max)]
     n_sat = min(n_max, 60_000)
+    # scan schedule per batch class the server will form (budget class x batch size), by measurement
+    qd = torch.as_tensor(qh[:max_batch], device="cuda")
+    tuned = {f"L{int(Lc)}_n{nb}": ix.autotune(qd[:nb], int(Lc), k)
+             for Lc in mix_L for nb in (32, 128, 512, 2048)}
     cfg = dict(k=k, slots=slots, max_batch=max_batch, L_max=int(mix_L.max()), device_bytes=device_bytes)
     serving.serve_continuous(ix, qh[:4096], Ls[:4096], np.zeros(4096), **cfg)  # warm-up
     sat = serving.serve_continuous(ix, qh[:n_sat], Ls[:n_sat], np.zeros(n_sat), **cfg)
@@ -486,6 +494,7 @@ def serve_block(ix, w, mix, k, seconds, seed=11, n_max=300_000, max_batch=4096, 
            "continuous": {"slots": slots, "max_batch": max_batch, "device_bytes": device_bytes,
                           "admission": "bpq_search_workspace_size of the batch at its largest L <= device_bytes / slots",
                           "batching": "one budget class (floor(log2 L)) per batch, oldest class first",
+                          "autotuned_work_items": tuned,
                           "saturated_qps": sat_qps, "saturated_stats": sat.stats, "loads": {}},
            "queue": {"max_batch": max_batch, "saturated_qps": sat_queue, "loads": {}}}
     for load in (0.5, 0.8):
@@ -523,6 +532,36 @@ def sweep(ix, queries, w, k, flush, stream, steps=3):
         res[f"speedup_L{L}"] = res[f"fbpq_L{L}"]["qps"] / res[f"recon_L{L}"]["qps"]
         res[f"speedup_tables_L{L}"] = res[f"fbpq_tables_L{L}"]["qps"] / res[f"recon_L{L}"]["qps"]
     return res
+
+
+def batching_block(ix, q, L, k, scorer, reps=50):
+    """One batch shape three ways, host wall time per batch (launches included): bpq_search; the same
+    search as one CUDA-graph launch; the graph of the autotuned scan schedule (bpq_autotune)."""
+    import torch
+    nq = q.shape[0]
+    Ls = L if hasattr(L, "__len__") else int(L)
+    ws = ix.workspace(nq, int(max(L) if hasattr(L, "__len__") else L), k, scorer)
+
+    def wall(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps * 1e3
+
+    t_search = wall(lambda: ix.search(q, Ls, k, scorer, workspace=ws))
+    g = ix.graph(q, Ls, k, scorer)
+    t_graph = wall(g.launch)
+    g.close()
+    W = ix.autotune(q, Ls, k, scorer)
+    g = ix.graph(q, Ls, k, scorer)
+    t_tuned = wall(g.launch)
+    g.close()
+    return {"nq": nq, "search_ms": t_search, "graph_ms": t_graph, "autotuned_work_item": W,
+            "autotuned_graph_ms": t_tuned}
 
 
 def exact_nn_gpu(q, w, mix, dev, chunk=2_000_000):
@@ -649,6 +688,7 @@ def config_block(name, serve_seconds=0.25):
             ms = timed(lambda: ixl.search(q, Ls, k, scorer), reps=5 if full else 1, warm=3 if full else 1)
             ids, _ = ixl.search(q, Ls, k, scorer)
             out[scorer] = {"qps": nq / (ms / 1e3), "ms": ms, "recall": recall_of(ids[:1000], nn)}
+        out["batching_hbpq"] = batching_block(ixl, q, Ls, k, "hbpq", reps=10)
         out["index_local"] = {"device_bytes": int(ixl.info().device_bytes)}
         del ixl
         ixg, out["build_global_s"] = build("global")
@@ -662,6 +702,7 @@ def config_block(name, serve_seconds=0.25):
             ids, _ = ixg.search(q, Ls, k, scorer)
             out[scorer] = {"qps": nq / (ms / 1e3), "ms": ms, "recall": recall_of(ids[:1000], nn)}
         out["hbpq_over_fbpq_time"] = out["hbpq"]["ms"] / out["fbpq"]["ms"]
+        out["batching_fbpq"] = batching_block(ixg, q, Ls, k, "fbpq", reps=10)
         out["index_global"] = {"device_bytes": int(ixg.info().device_bytes)}
     else:
         ix, out["build_s"] = build("global")

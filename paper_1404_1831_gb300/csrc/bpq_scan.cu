@@ -726,7 +726,7 @@ __device__ uint32_t block_cut(const uint64_t* a, int n, int k, int* red) {
 // the per-(query, half-cell) tables built by the HBPQ table kernel (read through
 // the cache from global memory; the table slots of the query come from its row
 // and column bitmaps), and no cross term is read.
-template <int M, int NT, int D, int U, int KW, int CH, bool HB>
+template <int M, int NT, int D, int U, int KW, int CH, bool HB, bool WQ>
 __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs a) {
   constexpr int NW = NT / 32, R = CH / NT, M2 = M / 2;
   static_assert(CH % NT == 0 && KW == 256, "shape (the exact prune keeps its payloads in the warp's 256 counters)");
@@ -753,16 +753,16 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
   uint32_t* hist = whist + w * 256;
   const char* lutb = reinterpret_cast<const char*>(lut);
 
-  // One unit of work per iteration: a whole query (a.items == NULL, CTAs strided
-  // over the queries), or a work item (q, cells c_lo .. c_hi - 1, partial slot)
-  // taken from the queue (persistent CTAs); a split query's items write partial
-  // top-k lists that merge_parts_kernel combines.
+  // One unit of work per iteration: a whole query (CTAs strided over the queries),
+  // or with WQ a work item (q, cells c_lo .. c_hi - 1, partial slot) taken from
+  // the queue (persistent CTAs); a split query's items write partial top-k lists
+  // that merge_parts_kernel combines.
   for (int64_t iter = blockIdx.x;; iter += gridDim.x) {
     __syncthreads();  // the previous unit's final list (in the table area) is written out
     int64_t q, out_row;
     int c_lo = 0, c_hi;
     bool part = false;
-    if (a.items) {
+    if constexpr (WQ) {
       if (threadIdx.x == 0) s_item = atomicAdd(a.item_counter, 1);
       __syncthreads();
       const int64_t it = s_item;
@@ -1287,17 +1287,17 @@ void run_fbpq_cfg(const ScanArgs& a, cudaStream_t st) {
   check_launch("fbpq scan kernel");
 }
 
-template <int M, int NT, int D, int U, int KW, int CH, bool HB = false>
-void run_fbpq_seg(const ScanArgs& a, cudaStream_t st) {
+template <int M, int NT, int D, int U, int KW, int CH, bool HB, bool WQ>
+void run_fbpq_seg_t(const ScanArgs& a, cudaStream_t st) {
   constexpr int NW = NT / 32;
   const size_t smem = (HB ? (size_t)4 * (MAX_T / 32) * 4 : (size_t)M * KSUB * 4) +
                       (size_t)NW * KW * 8 + (size_t)NW * 256 * 4 + (size_t)CH * 8 + (size_t)(CH + 2) * 4 +
                       (HB ? (size_t)CH * 8 : 0);
-  auto kern = fbpq_scan_seg_kernel<M, NT, D, U, KW, CH, HB>;
+  auto kern = fbpq_scan_seg_kernel<M, NT, D, U, KW, CH, HB, WQ>;
   BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // HB reads its tables through L1: shared memory for five CTAs (132 KB), the rest as cache
   if (HB) BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 57));
-  if (a.work_W > 0) {
+  if (WQ) {
     // persistent work-queue form: items, one resident wave of CTAs, merge of split queries
     BPQ_CHECK(a.items && a.n_items && a.item_counter && a.part_counter && a.merges && a.n_merges && a.part_ids &&
                   a.part_dists && a.k <= 128,
@@ -1317,6 +1317,14 @@ void run_fbpq_seg(const ScanArgs& a, cudaStream_t st) {
   const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
   kern<<<grid, NT, smem, st>>>(a);
   check_launch("fbpq segment scan kernel");
+}
+
+template <int M, int NT, int D, int U, int KW, int CH, bool HB = false>
+void run_fbpq_seg(const ScanArgs& a, cudaStream_t st) {
+  if (a.work_W > 0)
+    run_fbpq_seg_t<M, NT, D, U, KW, CH, HB, true>(a, st);
+  else
+    run_fbpq_seg_t<M, NT, D, U, KW, CH, HB, false>(a, st);
 }
 
 // Per-point cross terms and k <= 128: the warp-segment scan.  Otherwise the
