@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the Poisson serving measurement")
     ap.add_argument("--no-configs", action="store_true", help="skip the 100M / 1B configuration blocks")
-    ap.add_argument("--workload", choices=("sift10m", "c3", "c4", "c5"), default="sift10m",
+    ap.add_argument("--workload", choices=("sift10m", "c3", "c4", "c5", "gist"), default="sift10m",
                     help="c3: 100M, M=16, int8 shortlist; c4: 100M, local codebooks, uneven L; "
                          "c5: 1B points, serving (each prints its own JSON line)")
     ap.add_argument("--serve-seconds", type=float, default=0.25, help="arrival window per offered load")
@@ -450,7 +450,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_configs:
         # the 100M and 1B configurations, each on a fresh index (outside the timed region)
         out["configs"] = {}
-        for name in ("c3", "c4", "c5"):
+        for name in ("c3", "c4", "c5", "gist"):
             t0 = time.time()
             out["configs"][name] = config_block(name, args.serve_seconds)
             out["configs"][name]["wall_s"] = round(time.time() - t0, 1)
@@ -565,19 +565,25 @@ def batching_block(ix, q, L, k, scorer, reps=50):
 
 
 def exact_nn_gpu(q, w, mix, dev, chunk=2_000_000):
-    """Exact nearest neighbour of each query over the base points, by brute force in
-    FP32 with TF32 off (integer data: every partial sum is an integer below 2^24)."""
+    """Exact nearest neighbour of each query over the base points, by brute force with TF32 off: the inner
+    products are taken over blocks of at most 128 dimensions in FP32 (integer data in [0, 255]: every
+    partial sum is an integer below 2^24, so exact) and added in FP64."""
     import torch
 
     import synthdata as sd
     from synthdata import device as sdev
     n = q.shape[0]
-    qn = (q * q).sum(1, keepdim=True)
-    best = torch.full((n,), float("inf"), device=dev)
+    D = q.shape[1]
+    wide = D > 128
+    chunk = chunk // 4 if wide else chunk
+    ft = torch.float64 if wide else torch.float32
+    qn = (q.to(ft) * q.to(ft)).sum(1, keepdim=True)
+    best = torch.full((n,), float("inf"), dtype=ft, device=dev)
     arg = torch.zeros(n, dtype=torch.int64, device=dev)
     for s in range(0, w.n_base, chunk):
         x = sdev.points_cuda(mix, sd.STREAM_BASE, s, min(chunk, w.n_base - s), device=dev)
-        d = qn - 2.0 * (q @ x.T) + (x * x).sum(1)[None, :]
+        dot = sum((q[:, b:b + 128] @ x[:, b:b + 128].T).to(ft) for b in range(0, D, 128))
+        d = qn - 2.0 * dot + (x.to(ft) * x.to(ft)).sum(1)[None, :]
         m, a = d.min(1)
         upd = m < best
         best = torch.where(upd, m, best)
@@ -608,8 +614,8 @@ def config_block(name, serve_seconds=0.25):
     from synthdata import device as sdev
     dev = torch.device("cuda", 0)
     torch.backends.cuda.matmul.allow_tf32 = False
-    w = {"c3": sd.SIFT100M_M16, "c4": sd.SIFT100M, "c5": sd.SIFT1B}[name]
-    mix = sd.make_mixture(w.seed, w.n_comp)
+    w = {"c3": sd.SIFT100M_M16, "c4": sd.SIFT100M, "c5": sd.SIFT1B, "gist": sd.GIST50M}[name]
+    mix = sd.make_mixture(w.seed, w.n_comp, w.dim)
     learn = sdev.points_cuda(mix, sd.STREAM_LEARN, 0, w.n_learn, device=dev)
 
     def build(variant):
@@ -704,6 +710,25 @@ def config_block(name, serve_seconds=0.25):
         out["hbpq_over_fbpq_time"] = out["hbpq"]["ms"] / out["fbpq"]["ms"]
         out["batching_fbpq"] = batching_block(ixg, q, Ls, k, "fbpq", reps=10)
         out["index_global"] = {"device_bytes": int(ixg.info().device_bytes)}
+    elif name == "gist":
+        # the paper's GIST50M rows (Table FBPQ): FBPQ vs reconstruction at D = 384, 8-byte codes
+        ix, out["build_s"] = build("global")
+        del learn
+        out["index"] = {"device_bytes": int(ix.info().device_bytes)}
+        out["dim"] = w.dim
+        for L in w.L:
+            row = {}
+            for scorer in ("fbpq", "fbpq_tables", "recon"):
+                full = scorer != "recon"
+                ms = timed(lambda: ix.search(q, L, k, scorer), reps=3 if full else 1, warm=2 if full else 1)
+                row[scorer] = {"qps": nq / (ms / 1e3), "ms": ms}
+            ids, _ = ix.search(q[:1000], L, k, "fbpq")
+            ids_r, _ = ix.search(q[:1000], L, k, "recon")
+            row["recall_fbpq"] = recall_of(ids, nn)
+            row["recall_recon"] = recall_of(ids_r, nn)
+            row["speedup_fbpq_over_recon"] = row["recon"]["ms"] / row["fbpq"]["ms"]
+            out[f"L{L}"] = row
+        out["paper_cpu_speedup"] = {"L10000": 10.5, "L30000": 13.2, "L100000": 14.6}
     else:
         ix, out["build_s"] = build("global")
         del learn

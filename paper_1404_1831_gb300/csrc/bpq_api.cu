@@ -61,7 +61,7 @@ void check_params(const bpq_params* p) {
   BPQ_CHECK(p->variant == BPQ_VARIANT_GLOBAL || p->variant == BPQ_VARIANT_LOCAL, BPQ_EINVAL, "bad variant");
   BPQ_CHECK(p->kmeans_iters >= 0 && p->kmeans_iters <= 1000, BPQ_EINVAL, "kmeans_iters out of range");
   BPQ_CHECK(scan_supported(p->D, p->M), BPQ_EINVAL,
-            "this build supports (D, M) in {(128, 8), (128, 16), (32, 8), (8, 8)}");
+            "this build supports (D, M) in {(128, 8), (128, 16), (384, 8), (32, 8), (8, 8)}");
 }
 
 bpq_index* new_index(const bpq_params* p, int device) {

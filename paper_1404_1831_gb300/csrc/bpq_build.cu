@@ -423,7 +423,9 @@ void assign_dispatch(int dim, const float* X, int64_t ldx, int col, int64_t n, c
     case 4: assign_accum<4>(X, ldx, col, n, C, K, group, gstride, assign, sums, counts, st); break;
     case 8: assign_accum<8>(X, ldx, col, n, C, K, group, gstride, assign, sums, counts, st); break;
     case 16: assign_accum<16>(X, ldx, col, n, C, K, group, gstride, assign, sums, counts, st); break;
+    case 48: assign_accum<48>(X, ldx, col, n, C, K, group, gstride, assign, sums, counts, st); break;
     case 64: assign_accum<64>(X, ldx, col, n, C, K, group, gstride, assign, sums, counts, st); break;
+    case 192: assign_accum<192>(X, ldx, col, n, C, K, group, gstride, assign, sums, counts, st); break;
     default: throw Error(BPQ_EINVAL, "unsupported codeword dimension for K-means");
   }
 }
@@ -473,6 +475,7 @@ void launch_encode(const bpq_index& ix, const float* x, int64_t n, int32_t* cell
   else if (D == 128 && M == 16) encode_t<64, 8>(ix, x, n, cell, codes, st);
   else if (D == 32 && M == 8) encode_t<16, 4>(ix, x, n, cell, codes, st);
   else if (D == 8 && M == 8) encode_t<4, 1>(ix, x, n, cell, codes, st);
+  else if (D == 384 && M == 8) encode_t<192, 48>(ix, x, n, cell, codes, st);
   else throw Error(BPQ_EINVAL, "unsupported (D, M) for encoding");
 }
 
@@ -609,6 +612,7 @@ void train_codebooks(bpq_index& ix, const float* learn, int64_t n, cudaStream_t 
   gi.alloc((size_t)n * 4);
   gj.alloc((size_t)n * 4);
   if (h == 64) displacement<64>(learn, n, ix, disp.as<float>(), gi.as<int32_t>(), gj.as<int32_t>(), st);
+  else if (h == 192) displacement<192>(learn, n, ix, disp.as<float>(), gi.as<int32_t>(), gj.as<int32_t>(), st);
   else if (h == 16) displacement<16>(learn, n, ix, disp.as<float>(), gi.as<int32_t>(), gj.as<int32_t>(), st);
   else if (h == 4) displacement<4>(learn, n, ix, disp.as<float>(), gi.as<int32_t>(), gj.as<int32_t>(), st);
   else throw Error(BPQ_EINVAL, "unsupported D for training");

@@ -1150,7 +1150,9 @@ __global__ void __launch_bounds__(256) rescore_kernel(RescoreArgs r) {
 // Reconstruction scans (Multi-D-ADC and HBPQ): persistent CTAs, one query at a
 // time per CTA.
 // ---------------------------------------------------------------------------
-template <int M, int SUB, int KP, int NW, bool LOCAL>
+// RG: the global codebooks R are read through the cache instead of being staged
+// in shared memory (when they do not fit it, e.g. D/M = 48).
+template <int M, int SUB, int KP, int NW, bool LOCAL, bool RG>
 __global__ void __launch_bounds__(NW * 32) recon_scan_kernel(ScanArgs a) {
   constexpr int NT = NW * 32, D = M * SUB, H = D / 2, M2 = M / 2, CHR = 32, ILP = 2;
   constexpr int RS = SUB + 1;  // padded codeword stride
@@ -1169,7 +1171,7 @@ __global__ void __launch_bounds__(NW * 32) recon_scan_kernel(ScanArgs a) {
   __shared__ int64_t q_s;
   const int warp = threadIdx.x >> 5;
   const int k = a.k;
-  if (!LOCAL) {
+  if (!LOCAL && !RG) {
     for (int t = threadIdx.x; t < M * KSUB * SUB; t += NT) {
       const int row = t / SUB, d = t % SUB;
       Rs[row * RS + d] = a.R[t];
@@ -1244,6 +1246,13 @@ __global__ void __launch_bounds__(NW * 32) recon_scan_kernel(ScanArgs a) {
                 const float* w = (kk < M2)
                     ? a.Q + (((int64_t)c_i[c] * M2 + kk) * KSUB + b) * SUB
                     : a.S + (((int64_t)c_j[c] * M2 + kk - M2) * KSUB + b) * SUB;
+#pragma unroll
+                for (int d = 0; d < SUB; ++d) {
+                  const float t = r[kk * SUB + d] - __ldg(w + d);
+                  dist = fmaf(t, t, dist);
+                }
+              } else if (RG) {
+                const float* w = a.R + ((int64_t)kk * KSUB + b) * SUB;
 #pragma unroll
                 for (int d = 0; d < SUB; ++d) {
                   const float t = r[kk * SUB + d] - __ldg(w + d);
@@ -1345,10 +1354,12 @@ template <int M, int SUB, int KP, bool LOCAL>
 void run_recon(const ScanArgs& a, cudaStream_t st) {
   constexpr int NW = KP <= 128 ? 16 : (KP <= 256 ? 8 : (KP <= 512 ? 4 : 2));
   using TK = WarpTopK<KP>;
-  const size_t smem = (size_t)NW * TK::AREA * 8 + (size_t)32 * (M * SUB + 1) * 4 +
-                      (LOCAL ? 0 : (size_t)M * KSUB * (SUB + 1) * 4);
-  BPQ_CHECK(smem <= 227 * 1024, BPQ_EINVAL, "reconstruction scan: codebooks do not fit shared memory");
-  auto kern = recon_scan_kernel<M, SUB, KP, NW, LOCAL>;
+  // the global codebooks go to shared memory when they fit beside the rest
+  constexpr size_t BASE = (size_t)NW * TK::AREA * 8 + (size_t)32 * (M * SUB + 1) * 4;
+  constexpr bool RG = !LOCAL && BASE + (size_t)M * KSUB * (SUB + 1) * 4 > 200 * 1024;
+  const size_t smem = BASE + ((LOCAL || RG) ? 0 : (size_t)M * KSUB * (SUB + 1) * 4);
+  BPQ_CHECK(smem <= 227 * 1024, BPQ_EINVAL, "reconstruction scan: shape too large for shared memory");
+  auto kern = recon_scan_kernel<M, SUB, KP, NW, LOCAL, RG>;
   BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   BPQ_CUDA(cudaMemsetAsync(a.qcounter, 0, sizeof(int32_t), st));
   const int grid = (int)std::min<int64_t>(a.nq, (int64_t)a.sm_count);
@@ -1390,7 +1401,7 @@ void dispatch_k(const ScanArgs& a, int scorer, cudaStream_t st) {
 }  // namespace
 
 bool scan_supported(int D, int M) {
-  return (D == 128 && (M == 8 || M == 16)) || (D == 32 && M == 8) || (D == 8 && M == 8);
+  return (D == 128 && (M == 8 || M == 16)) || (D == 32 && M == 8) || (D == 8 && M == 8) || (D == 384 && M == 8);
 }
 
 void launch_scan_reduced(const ScanArgs& a, bool f16, cudaStream_t st) {
@@ -1422,6 +1433,7 @@ void launch_scan(const ScanArgs& a, int scorer, cudaStream_t st) {
   else if (D == 128 && M == 16) dispatch_k<16, 8>(a, scorer, st);
   else if (D == 32 && M == 8) dispatch_k<8, 4>(a, scorer, st);
   else if (D == 8 && M == 8) dispatch_k<8, 1>(a, scorer, st);
+  else if (D == 384 && M == 8) dispatch_k<8, 48>(a, scorer, st);
   else throw Error(BPQ_EINVAL, "unsupported (D, M) for the scan kernels");
 }
 

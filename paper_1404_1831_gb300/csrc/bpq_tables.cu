@@ -69,10 +69,10 @@ __global__ void __launch_bounds__(128) tc_table_kernel(const float* __restrict__
   unsigned char* sA = tsm;
   unsigned char* sB = tsm + TC_M * kpad * 2;
   int bad = 0;
-  if (((pr.dim | lda | pr.a_off) & 3) == 0) {  // query slices as float4 groups (kpad is a power of two)
-    const int sh = __ffs(kpad >> 2) - 1;
-    for (int e = tid; e < (TC_M * kpad) >> 2; e += 128) {
-      const int r = e >> sh, k = (e & ((kpad >> 2) - 1)) << 2;
+  if (((pr.dim | lda | pr.a_off) & 3) == 0) {  // query slices as float4 groups (kpad is a multiple of 16)
+    const int q4 = kpad >> 2;
+    for (int e = tid; e < TC_M * q4; e += 128) {
+      const int r = e / q4, k = (e - r * q4) << 2;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (a0 + r < na && k < pr.dim) v = *reinterpret_cast<const float4*>(A + (int64_t)(a0 + r) * lda + pr.a_off + k);
       const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
@@ -92,9 +92,9 @@ __global__ void __launch_bounds__(128) tc_table_kernel(const float* __restrict__
     }
   }
   {  // codewords: one 16-byte core row per step
-    const int sh = __ffs(kpad >> 3) - 1;
-    for (int e = tid; e < (nt * kpad) >> 3; e += 128) {
-      const int r = e >> sh, k = (e & ((kpad >> 3) - 1)) << 3;
+    const int q8 = kpad >> 3;
+    for (int e = tid; e < nt * q8; e += 128) {
+      const int r = e / q8, k = (e - r * q8) << 3;
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
       if (n0 + r < pr.nb) v = *reinterpret_cast<const uint4*>(pr.Bb + (int64_t)(n0 + r) * kpad + k);
       *reinterpret_cast<uint4*>(sB + core_off(r, k, KB)) = v;
@@ -358,8 +358,7 @@ void build_fbpq_tables(bpq_index& ix, cudaStream_t st) {
   // tensor-core operands of the query tables
   ix.kh = (ix.h + 15) & ~15;
   ix.ks = (ix.s + 15) & ~15;
-  BPQ_CHECK(ix.kh <= 64 && ix.ks <= 64 && (ix.kh & (ix.kh - 1)) == 0 && (ix.ks & (ix.ks - 1)) == 0, BPQ_EINVAL,
-            "table operand widths must be powers of two up to 64");
+  BPQ_CHECK(ix.kh <= 192 && ix.ks <= 64, BPQ_EINVAL, "table operand widths: D/2 <= 192 and D/M <= 64");
   const int64_t nR = (int64_t)ix.p.M * KSUB;
   ix.C1b.alloc((size_t)T * ix.kh * 2);
   ix.C2b.alloc((size_t)T * ix.kh * 2);

@@ -28,7 +28,9 @@ Parameter stream ``PARAM_STREAM``; counter n = c for component c:
   * weight W_c = 2^20 + (word1 >> 43)                            in [2^20, 3*2^20)
   * mean mu_c[d] = min(255, 12*g + ((word(2+d) >> 16) % 24)), where g is the
     number of consecutive low-order one bits of word(2+d) (capped at 8), a
-    Geometric(1/2) draw: SIFT-like mass near zero with a long tail.
+    Geometric(1/2) draw: SIFT-like mass near zero with a long tail.  (For
+    d >= 254 the word is word(2 + d mod 254) of counter c + 2^38 * floor(d / 254),
+    so that w stays below 2^8.)
   * cum[c] = floor(2^32 * sum_{c'<=c} W_c' / sum W)              (cum[-1] = 2^32)
 and counter n = 2^39 + d for the shared loadings B[d][f] = (word f >> 32) % 7 - 3.
 
@@ -129,7 +131,9 @@ def make_mixture(seed: int, n_comp: int, dim: int = 128) -> Mixture:
     for i in range(n_comp):
         run += weight[i]
         cum[i] = (run << 32) // total
-    wd = draw(seed, PARAM_STREAM, c[:, None], 2 + np.arange(dim, dtype=_U64)[None, :])
+    dd = np.arange(dim, dtype=_U64)
+    wd = draw(seed, PARAM_STREAM, c[:, None] + (dd[None, :] // _U64(254)) * (_U64(1) << _U64(38)),
+              _U64(2) + dd[None, :] % _U64(254))
     g = np.zeros(wd.shape, dtype=np.int32)
     alive = np.ones(wd.shape, dtype=bool)
     for b in range(8):
@@ -194,4 +198,10 @@ SIFT100M = Workload("sift100m-T1024-M8", n_base=100_000_000, n_learn=1_024_000, 
                     n_comp=1024, T=1024, M=8, L=(1_000, 100_000), k=100)
 SIFT1B = Workload("sift1b-T1024-M8", n_base=1_000_000_000, n_learn=1_024_000, n_query=10_000,
                   n_comp=4096, T=1024, M=8, L=(1_000, 10_000, 100_000), k=100)
-WORKLOADS = {w.name: w for w in (TINY, SIFT10M, SIFT100M_M16, SIFT100M, SIFT1B)}
+# GIST-shaped (D = 384, 8-byte codes, T = 1024 as for GIST50M): the same generator in 384
+# dimensions; and a small case of the same shape for parity tests.
+GIST50M = Workload("gist50m-T1024-M8", n_base=50_000_000, n_learn=1_024_000, n_query=10_000,
+                   n_comp=1024, T=1024, M=8, L=(10_000, 30_000, 100_000), k=100, dim=384)
+TINY_GIST = Workload("tiny-gist-50k-T32-M8", n_base=50_000, n_learn=20_000, n_query=30,
+                     n_comp=64, T=32, M=8, L=(5_000,), k=50, dim=384, kmeans_iters=4)
+WORKLOADS = {w.name: w for w in (TINY, SIFT10M, SIFT100M_M16, SIFT100M, SIFT1B, GIST50M, TINY_GIST)}
