@@ -88,39 +88,66 @@ def _oracle_encode_chunk(task):
     return O.encode_multi_d_adc(x, cb)
 
 
-def _oracle_worker(w, L, k, seconds, nq_max, out_q, procs):
-    """Builds the oracle's own index of the workload, then times its search."""
+_ORACLE_INDEX = None  # the timing processes' index (inherited by fork from the oracle worker)
+
+
+def _oracle_time_slice(task):
+    """Times the oracle's search of queries [a, b) (one process, one core)."""
+    import synthdata as sd
+    from oracle import bpq_oracle as O
+    w, L, k, a, b, seconds = task
+    mix = sd.make_mixture(w.seed, w.n_comp)
+    queries = sd.points(mix, sd.STREAM_QUERY, a, b - a)
+    O.search_one(_ORACLE_INDEX, queries[0], L, k, "fbpq")  # warm caches
+    times, t1 = [], time.time()
+    for n in range(b - a):
+        if time.time() - t1 >= seconds:
+            break
+        s0 = time.time()
+        O.search_one(_ORACLE_INDEX, queries[n], L, k, "fbpq")
+        times.append(time.time() - s0)
+    return times
+
+
+def _oracle_worker(w, L, k, seconds, nq_max, out_q, procs, cb_arrays):
+    """Builds the oracle's index of the workload (with the given codebooks, else its own
+    training), then times its search on one core and on `procs` cores at once.  Runs in a
+    spawned process that never touches the GPU, so it may fork its timing processes."""
+    global _ORACLE_INDEX
     import numpy as np
 
     import synthdata as sd
     from oracle import bpq_oracle as O
     t0 = time.time()
     mix = sd.make_mixture(w.seed, w.n_comp)
-    learn = sd.points(mix, sd.STREAM_LEARN, 0, min(ORACLE_LEARN, w.n_learn))
-    cb = O.train_multi_d_adc(learn, w.T, w.M, ORACLE_ITERS)
+    if cb_arrays is not None:
+        cb = O.Codebooks(D=w.dim, T=w.T, M=w.M, **{n: np.asarray(v, dtype=np.int64) for n, v in cb_arrays.items()})
+    else:
+        learn = sd.points(mix, sd.STREAM_LEARN, 0, min(ORACLE_LEARN, w.n_learn))
+        cb = O.train_multi_d_adc(learn, w.T, w.M, ORACLE_ITERS)
     step = 250_000
     tasks = [(w.seed, w.n_comp, s, min(step, w.n_base - s), cb) for s in range(0, w.n_base, step)]
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(procs) as pool:
+    with mp.get_context("fork").Pool(procs) as pool:
         parts = pool.map(_oracle_encode_chunk, tasks)
     cells = np.concatenate([p[0] for p in parts])
     codes = np.concatenate([p[1] for p in parts])
-    index = O.OracleIndex(cb=cb, lists=O.build_lists(cells, codes, np.arange(w.n_base), w.T), variant="global",
-                          tables=O.fbpq_tables(cb))
+    _ORACLE_INDEX = O.OracleIndex(cb=cb, lists=O.build_lists(cells, codes, np.arange(w.n_base), w.T),
+                                  variant="global", tables=O.fbpq_tables(cb))
     build_s = time.time() - t0
-    queries = sd.points(mix, sd.STREAM_QUERY, 0, nq_max)
-    O.search_one(index, queries[0], L, k, "fbpq")  # warm caches
-    done, t1 = 0, time.time()
-    times = []
-    while done < nq_max and (time.time() - t1) < seconds:
-        s = time.time()
-        O.search_one(index, queries[done], L, k, "fbpq")
-        times.append(time.time() - s)
-        done += 1
-    out_q.put(dict(n=done, seconds=sum(times), times=times, build_s=build_s))
+    one = _oracle_time_slice((w, L, k, 0, nq_max, seconds))
+    res = dict(n=len(one), seconds=sum(one), times=one, build_s=build_s)
+    if procs > 1:  # P processes over disjoint query slices, all at once: aggregate queries/s
+        per = 100
+        slices = [(w, L, k, nq_max + i * per, nq_max + (i + 1) * per, seconds) for i in range(procs)]
+        t1 = time.time()
+        with mp.get_context("fork").Pool(procs) as pool:
+            parts = pool.map(_oracle_time_slice, slices)
+        wall = time.time() - t1
+        res["multi"] = dict(procs=procs, queries=sum(len(p) for p in parts), wall_s=wall)
+    out_q.put(res)
 
 
-def run_oracle(w, L, k, seconds, nq_max=200):
+def run_oracle(w, L, k, seconds, nq_max=200, cb_arrays=None, multi=True):
     """Oracle search timing in a spawned process with single-threaded BLAS."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
@@ -129,7 +156,8 @@ def run_oracle(w, L, k, seconds, nq_max=200):
         os.environ[v] = "1"
     procs = max(1, min(16, os.cpu_count() or 1))
     try:
-        p = ctx.Process(target=_oracle_worker, args=(w, L, k, seconds, nq_max, q, procs))
+        p = ctx.Process(target=_oracle_worker,
+                        args=(w, L, k, seconds, nq_max, q, procs if multi else 1, cb_arrays))
         p.start()
         res = q.get()
         p.join()
@@ -142,10 +170,11 @@ def run_oracle(w, L, k, seconds, nq_max=200):
     return res
 
 
-def oracle_sample_text(w, L, n):
+def oracle_sample_text(w, L, n, own=True):
+    cbs = (f"the oracle's own codebooks ({ORACLE_ITERS} Lloyd iterations on {ORACLE_LEARN} learn points)" if own
+           else "the GPU arm's codebooks (the same index)")
     return (f"{n} queries of the {w.name} workload (N={w.n_base}, T={w.T}, M={w.M}) at L={L}, k=100, FBPQ "
-            f"scoring, one at a time on one core, against the oracle's own index (codebooks from "
-            f"{ORACLE_ITERS} Lloyd iterations on {ORACLE_LEARN} learn points)")
+            f"scoring, one at a time on one core, on the oracle's lists built with {cbs}")
 
 
 # ---------------------------------------------------------------------------
@@ -441,6 +470,11 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_serve:
         out["serve"] = serve_block(ix, w, mix, k, args.serve_seconds)
 
+    cb_arrays = None
+    if want_cpu:  # the CPU baseline searches the same index: the GPU arm's codebooks
+        a = ix.arrays()
+        cb_arrays = {n: a[n].cpu().numpy() for n in ("C1", "C2", "R")}
+        del a
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -456,11 +490,18 @@ def run_ours(args):
             out["configs"][name]["wall_s"] = round(time.time() - t0, 1)
             torch.cuda.empty_cache()
     if want_cpu:
-        res = run_oracle(w, L, k, args.oracle_seconds)
+        res = run_oracle(w, L, k, args.oracle_seconds, cb_arrays=cb_arrays)
         out["cpu_baseline"] = {"value": res["n"] / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": oracle_sample_text(w, L, res["n"]),
+                               "sample": oracle_sample_text(w, L, res["n"], own=False),
+                               "same_codebooks_as_gpu": True,
                                "ms_per_query_median": 1e3 * statistics.median(res["times"]),
                                "oracle_index_build_s": round(res["build_s"], 1)}
+        if "multi" in res:
+            m = res["multi"]
+            out["cpu_baseline"]["all_cores"] = {
+                "value": m["queries"] / m["wall_s"], "unit": UNIT, "cores": m["procs"],
+                "sample": f"{m['procs']} processes at once, each timing its own slice of the query stream "
+                          f"(disjoint queries), for about {args.oracle_seconds:.0f} s; aggregate queries/s"}
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -793,7 +834,7 @@ def run_reference(args):
     w = workload(args)
     per_step = 2
     total = per_step * (args.steps + args.warmup)
-    res = run_oracle(w, args.L, args.k, seconds=1e9, nq_max=total)
+    res = run_oracle(w, args.L, args.k, seconds=1e9, nq_max=total, multi=False)
     times = res["times"][per_step * args.warmup:]
     seconds = sum(times)
     value = len(times) / seconds
