@@ -132,10 +132,39 @@ class Codebooks:
     R: np.ndarray             # (M, 256, D/M) global residual codebooks R_1..R_M
     Q: np.ndarray | None = None  # (T, M/2, 256, D/M) HBPQ local codebooks Q^i_k
     S: np.ndarray | None = None  # (T, M/2, 256, D/M) HBPQ local codebooks S^j_k
+    # OPQ ("optimized" variants, §2.3 / §3.2): orthogonal rotations, FP64.  rot0 (D, D)
+    # acts on the vectors before the coarse quantization; rot1, rot2 (D/2, D/2) act on
+    # the two halves of the displacement before the residual PQ.  None: no rotation.
+    rot0: np.ndarray | None = None
+    rot1: np.ndarray | None = None
+    rot2: np.ndarray | None = None
 
     @property
     def sub(self):
         return self.D // self.M
+
+    @property
+    def rotated(self):
+        return self.rot0 is not None
+
+    def coarse_space(self, X):
+        """x' = rot0 x (the space of the coarse codebooks C^1, C^2)."""
+        X = np.asarray(X)
+        return X @ self.rot0.T if self.rotated else X
+
+    def residual_space(self, V):
+        """[rot1 v^1; rot2 v^2] for vectors of the coarse space (the space of R_k)."""
+        V = np.asarray(V)
+        if not self.rotated:
+            return V
+        h = self.D // 2
+        return np.concatenate([V[..., :h] @ self.rot1.T, V[..., h:] @ self.rot2.T], axis=-1)
+
+    def residual_centroids(self):
+        """The coarse centroids in the residual space, [rot1 c^1_i], [rot2 c^2_j]."""
+        if not self.rotated:
+            return self.C1, self.C2
+        return (np.asarray(self.C1, np.float64) @ self.rot1.T, np.asarray(self.C2, np.float64) @ self.rot2.T)
 
 
 def check_shape(D, T, M):
@@ -166,6 +195,77 @@ def train_multi_d_adc(learn, T, M, iters):
     return Codebooks(D=D, T=T, M=M, C1=C1, C2=C2, R=R)
 
 
+def round_half_up(V):
+    """Nearest integer, halves up: floor(v + 1/2) (the integer-grid reading)."""
+    return np.floor(np.asarray(V, np.float64) + 0.5).astype(np.int64)
+
+
+def allocate_eigenvalues(lam, groups):
+    """Eigenvalue allocation of parametric OPQ (Ge et al., "Optimized Product
+    Quantization", 2013): eigenvalues in descending order (ties by index) are dealt
+    to `groups` subspaces of len(lam)/groups dimensions each; each goes to the
+    non-full subspace with the smallest sum of log eigenvalues so far (ties to the
+    lower subspace), which balances the products of the subspaces' variances.
+    Returns, per subspace, the eigenvalue indices in the order they were dealt."""
+    lam = np.asarray(lam, np.float64)
+    d = len(lam)
+    cap = d // groups
+    order = sorted(range(d), key=lambda i: (-lam[i], i))
+    buckets = [[] for _ in range(groups)]
+    logsum = [0.0] * groups
+    for i in order:
+        b = min((g for g in range(groups) if len(buckets[g]) < cap), key=lambda g: (logsum[g], g))
+        buckets[b].append(i)
+        logsum[b] += float(np.log(max(lam[i], 1e-12)))
+    return buckets
+
+
+def opq_rotation(X, groups):
+    """Parametric OPQ rotation for `groups` subspaces: the eigenvectors of the
+    covariance of X (FP64), arranged by allocate_eigenvalues so that subspace g
+    holds rows g*d/groups .. (g+1)*d/groups - 1.  Each eigenvector's largest-magnitude
+    component is made positive (first such index on ties)."""
+    X = np.asarray(X, np.float64)
+    mu = X.mean(0)
+    C = (X.T @ X) / len(X) - np.outer(mu, mu)
+    lam, V = np.linalg.eigh(C)
+    rows = []
+    for b in allocate_eigenvalues(lam, groups):
+        for i in b:
+            v = V[:, i]
+            if v[int(np.argmax(np.abs(v)))] < 0:
+                v = -v
+            rows.append(v)
+    return np.stack(rows)
+
+
+def train_opq(learn, T, M, iters, rotations=None):
+    """OMulti-D-OADC codebooks (§2.3, the optimized Multi-D-ADC of the paper's
+    experiments; the learner is the parametric OPQ solution): rot0 from the learn set
+    for the two halves, coarse codebooks on the rotated learn set, then rot1, rot2 from
+    the two halves of the displacements for M/2 subspaces each, and R_k on the rotated
+    displacements.  Reading (integer grid): the rotated learn vectors and the rotated
+    displacements are rounded half up before K-means, so every codebook is integral
+    in its (rotated) space.  rotations: (rot0, rot1, rot2) to use instead of learning."""
+    learn = np.asarray(learn, dtype=np.int64)
+    D = learn.shape[1]
+    check_shape(D, T, M)
+    h, s, m2 = D // 2, D // M, M // 2
+    rot0 = rotations[0] if rotations is not None else opq_rotation(learn, 2)
+    lp = round_half_up(learn @ rot0.T)
+    C1, _ = kmeans(lp[:, :h], T, iters)
+    C2, _ = kmeans(lp[:, h:], T, iters)
+    i, j = coarse_cells(lp, C1, C2)
+    disp = lp - np.concatenate([C1[i], C2[j]], axis=1)
+    if rotations is not None:
+        rot1, rot2 = rotations[1], rotations[2]
+    else:
+        rot1, rot2 = opq_rotation(disp[:, :h], m2), opq_rotation(disp[:, h:], m2)
+    dr = np.concatenate([round_half_up(disp[:, :h] @ rot1.T), round_half_up(disp[:, h:] @ rot2.T)], axis=1)
+    R = np.stack([kmeans(dr[:, k * s:(k + 1) * s], KSUB, iters)[0] for k in range(M)])
+    return Codebooks(D=D, T=T, M=M, C1=C1, C2=C2, R=R, rot0=rot0, rot1=rot1, rot2=rot2)
+
+
 def train_hbpq_local(learn, cb: Codebooks, iters):
     """HBPQ local codebooks of §3.2.  For each first-half Voronoi cell U_i (Eq. 10)
     the M/2 codebooks Q^i_k are learned on the displacements p^1 - c^1_i of the learn
@@ -173,6 +273,8 @@ def train_hbpq_local(learn, cb: Codebooks, iters):
     Reading: each local codebook starts from the global R_k of the same
     sub-quantizer; a half-cell with no learn points keeps the global codebook."""
     learn = np.asarray(learn, dtype=np.int64)
+    if cb.rotated:
+        raise ValueError("local codebooks are built for unrotated codebooks")
     D, T, M, s = cb.D, cb.T, cb.M, cb.sub
     h, m2 = D // 2, M // 2
     i, j = coarse_cells(learn, cb.C1, cb.C2)
@@ -197,11 +299,14 @@ def train_hbpq_local(learn, cb: Codebooks, iters):
 
 def encode_multi_d_adc(X, cb: Codebooks):
     """Cell and PQ code of each point (§2.3.2): d = x - [c^1_i; c^2_j] (Eq. 6) is
-    encoded with R_1..R_M, code k = argmin_t ||d_k - R_k[t]||^2."""
+    encoded with R_1..R_M, code k = argmin_t ||d_k - R_k[t]||^2.  With OPQ rotations
+    the cell comes from x' = rot0 x and the code from the rotated displacement
+    [rot1 d^1; rot2 d^2] (FP64; no rounding of points)."""
     X = np.asarray(X, dtype=np.int64)
     s = cb.sub
-    i, j = coarse_cells(X, cb.C1, cb.C2)
-    disp = X - np.concatenate([cb.C1[i], cb.C2[j]], axis=1)
+    Xc = cb.coarse_space(X)
+    i, j = coarse_cells(Xc, cb.C1, cb.C2)
+    disp = cb.residual_space(Xc - np.concatenate([cb.C1[i], cb.C2[j]], axis=1))
     codes = np.stack([nearest(disp[:, k * s:(k + 1) * s], cb.R[k]) for k in range(cb.M)], axis=1)
     return i * cb.T + j, codes.astype(np.uint8)
 
@@ -256,8 +361,9 @@ def build_lists(cells, codes, ids, T):
 
 
 def coarse_distances(q, cb: Codebooks):
-    """d1[i] = ||q^1 - c^1_i||^2 and d2[j] = ||q^2 - c^2_j||^2 for one query."""
-    q = np.asarray(q, dtype=np.float64)
+    """d1[i] = ||q^1 - c^1_i||^2 and d2[j] = ||q^2 - c^2_j||^2 for one query (with OPQ,
+    of q' = rot0 q)."""
+    q = cb.coarse_space(np.asarray(q, dtype=np.float64))
     h = cb.D // 2
     return sq_dists(q[None, :h], cb.C1)[0], sq_dists(q[None, h:], cb.C2)[0]
 
@@ -328,11 +434,17 @@ def candidates(cells_visited, lists: Lists):
 
 
 def reconstruct(cb: Codebooks, cell, codes):
-    """Approximation of Eq. 7: x ~ [c^1_i; c^2_j] + [r_1; ...; r_M] with global R_k."""
+    """Approximation of Eq. 7: x ~ [c^1_i; c^2_j] + [r_1; ...; r_M] with global R_k.
+    With OPQ rotations, in the original space: x ~ rot0^T ([c^1_i; c^2_j] +
+    [rot1^T r^1; rot2^T r^2])."""
     cell = np.asarray(cell, dtype=np.int64)
     codes = np.asarray(codes, dtype=np.int64)
     i, j = cell // cb.T, cell % cb.T
     r = np.concatenate([cb.R[k][codes[:, k]] for k in range(cb.M)], axis=1)
+    if cb.rotated:
+        h = cb.D // 2
+        r = np.concatenate([r[:, :h] @ cb.rot1, r[:, h:] @ cb.rot2], axis=1).astype(np.float64)
+        return (np.concatenate([cb.C1[i], cb.C2[j]], axis=1).astype(np.float64) + r) @ cb.rot0
     return np.concatenate([cb.C1[i], cb.C2[j]], axis=1).astype(np.float64) + r
 
 
@@ -409,12 +521,16 @@ class FbpqTables:
 
 
 def fbpq_tables(cb: Codebooks):
+    """With OPQ rotations the dot products of Eq. 9 are taken in the residual space,
+    with the rotated coarse centroids [rot1 c^1_i], [rot2 c^2_j] (the norms are
+    unchanged by the rotations)."""
     s, m2 = cb.sub, cb.M // 2
     C1 = cb.C1.astype(np.float64)
     C2 = cb.C2.astype(np.float64)
     R = cb.R.astype(np.float64)
-    X1 = np.stack([C1[:, k * s:(k + 1) * s] @ R[k].T for k in range(m2)], axis=1)
-    X2 = np.stack([C2[:, k * s:(k + 1) * s] @ R[m2 + k].T for k in range(m2)], axis=1)
+    C1r, C2r = (np.asarray(c, np.float64) for c in cb.residual_centroids())
+    X1 = np.stack([C1r[:, k * s:(k + 1) * s] @ R[k].T for k in range(m2)], axis=1)
+    X2 = np.stack([C2r[:, k * s:(k + 1) * s] @ R[m2 + k].T for k in range(m2)], axis=1)
     return FbpqTables(n1=(C1 * C1).sum(1), n2=(C2 * C2).sum(1), nR=(R * R).sum(2), X1=X1, X2=X2)
 
 
@@ -426,15 +542,19 @@ def dist_fbpq(q, cb: Codebooks, tab: FbpqTables, cell, codes):
           + 2 sum_{k<=M/2} <c^1_i, r_k> + 2 sum_{k>M/2} <c^2_j, r_k>
 
     The query tables <q^1, c^1_i>, <q^2, c^2_j> and <q_k, R_k[t]> are built once
-    per query (§3.1) and every term is then a lookup, O(M) per point."""
-    q = np.asarray(q, np.float64)
+    per query (§3.1) and every term is then a lookup, O(M) per point.  With OPQ
+    rotations the coarse terms use q' = rot0 q and the residual terms the rotated
+    query [rot1 q'^1; rot2 q'^2] (the rotations are orthogonal, so the sum is the
+    distance to the reconstruction in the original space)."""
+    q = cb.coarse_space(np.asarray(q, np.float64))
+    qr_vec = cb.residual_space(q)
     cell = np.asarray(cell, dtype=np.int64)
     codes = np.asarray(codes, dtype=np.int64)
     s, h, m2 = cb.sub, cb.D // 2, cb.M // 2
     i, j = cell // cb.T, cell % cb.T
     qc1 = cb.C1.astype(np.float64) @ q[:h]
     qc2 = cb.C2.astype(np.float64) @ q[h:]
-    qr = np.stack([cb.R[k].astype(np.float64) @ q[k * s:(k + 1) * s] for k in range(cb.M)])
+    qr = np.stack([cb.R[k].astype(np.float64) @ qr_vec[k * s:(k + 1) * s] for k in range(cb.M)])
     ks = np.arange(cb.M)
     dot_qr = qr[ks[None, :], codes].sum(1)
     norm_r = tab.nR[ks[None, :], codes].sum(1)
@@ -454,8 +574,9 @@ def dist_fbpq(q, cb: Codebooks, tab: FbpqTables, cell, codes):
 
 def pq_table(q, cb: Codebooks):
     """Per-query PQ table of §3.1: lut[k][t] = ||R_k[t]||^2 - 2<q_k, R_k[t]>, the
-    query term of Eq. 8 plus the codeword norm of Eq. 9, shape (M, 256)."""
-    q = np.asarray(q, np.float64)
+    query term of Eq. 8 plus the codeword norm of Eq. 9, shape (M, 256) (with OPQ,
+    of the rotated query [rot1 q'^1; rot2 q'^2], q' = rot0 q)."""
+    q = cb.residual_space(cb.coarse_space(np.asarray(q, np.float64)))
     s = cb.sub
     R = cb.R.astype(np.float64)
     return np.stack([(R[k] * R[k]).sum(1) - 2.0 * (R[k] @ q[k * s:(k + 1) * s]) for k in range(cb.M)])
