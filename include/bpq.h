@@ -85,6 +85,10 @@ typedef struct {
   int32_t ksub;         /* codewords per PQ codebook; must be 256 (one byte per index) */
   int32_t variant;      /* BPQ_VARIANT_* */
   int32_t kmeans_iters; /* Lloyd iterations for bpq_train_load */
+  int32_t opq;          /* 1: OPQ rotations (the "optimized" OMulti-D-OADC of §2.3; global
+                           variant only): rot0 (D x D) on vectors before the coarse
+                           quantization, rot1 / rot2 (D/2 x D/2) on the displacement halves
+                           before the residual PQ; 0: none */
 } bpq_params;
 
 typedef struct {
@@ -463,6 +467,19 @@ int bpq_graph_create(bpq_graph** out, const bpq_index* idx, const float* queries
 int bpq_graph_set_budgets(bpq_graph* g, const int64_t* L_host);
 int bpq_graph_launch(bpq_graph* g, void* stream);
 void bpq_graph_free(bpq_graph* g);
+
+/*
+ * bpq_set_rotations — the OPQ rotations of an index made by bpq_create with
+ * params.opq = 1 (its codebooks C^1, C^2 then live in the space of rot0 x and R_k in
+ * the space of [rot1 d^1; rot2 d^2]); before any point is added.  R0: D x D, R1, R2:
+ * D/2 x D/2, row-major FP64 host arrays (orthogonal; copied).  bpq_train_load with
+ * params.opq = 1 learns them instead (parametric OPQ: covariance eigenvectors dealt
+ * to the subspaces by balanced log-eigenvalue sums; the rotated learn vectors and
+ * displacements are rounded half up before K-means).  Errors: BPQ_EINVAL, BPQ_ESTATE.
+ */
+int bpq_set_rotations(bpq_index* idx, const double* R0_host, const double* R1_host, const double* R2_host);
+/* bpq_get_rotations — copies an OPQ index's rotations to host arrays (sizes as above). */
+int bpq_get_rotations(const bpq_index* idx, double* R0_host, double* R1_host, double* R2_host);
 
 /* bpq_info / bpq_arrays — sizes and read-only device views (see the structs). */
 int bpq_get_info(const bpq_index* idx, bpq_info* out);

@@ -30,7 +30,7 @@ class BpqError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("D", ctypes.c_int32), ("T", ctypes.c_int32), ("M", ctypes.c_int32), ("ksub", ctypes.c_int32),
-                ("variant", ctypes.c_int32), ("kmeans_iters", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("kmeans_iters", ctypes.c_int32), ("opq", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -77,6 +77,8 @@ _SIGS = {
     "bpq_search_status": (ctypes.c_int, [_P, _P, _P]),
     "bpq_set_hbpq_table_budget": (ctypes.c_int, [_P, ctypes.c_double]),
     "bpq_set_scan_work_size": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "bpq_set_rotations": (ctypes.c_int, [_P, _P, _P, _P]),
+    "bpq_get_rotations": (ctypes.c_int, [_P, _P, _P, _P]),
     "bpq_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P,
                                     _P, _P, _P]),
     "bpq_graph_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, _P, ctypes.c_int64, _P, ctypes.c_int64,
@@ -173,33 +175,39 @@ class Index:
 
     # -- construction ---------------------------------------------------------
     @staticmethod
-    def _params(D, T, M, variant, iters):
-        return Params(D=D, T=T, M=M, ksub=256, variant=variant, kmeans_iters=iters)
+    def _params(D, T, M, variant, iters, opq=False):
+        return Params(D=D, T=T, M=M, ksub=256, variant=variant, kmeans_iters=iters, opq=1 if opq else 0)
 
     @classmethod
-    def create(cls, C1, C2, R, Q=None, S=None, device=0):
-        """Index from host codebooks: C1, C2 (T, D/2); R (M, 256, D/M); Q, S (T, M/2, 256, D/M) for HBPQ."""
+    def create(cls, C1, C2, R, Q=None, S=None, device=0, rotations=None):
+        """Index from host codebooks: C1, C2 (T, D/2); R (M, 256, D/M); Q, S (T, M/2, 256, D/M) for HBPQ;
+        rotations = (R0 (D, D), R1, R2 (D/2, D/2)) for an OPQ index (codebooks in the rotated spaces)."""
         C1 = np.ascontiguousarray(C1, dtype=np.float32)
         C2 = np.ascontiguousarray(C2, dtype=np.float32)
         R = np.ascontiguousarray(R, dtype=np.float32)
         T, h = C1.shape
         M = R.shape[0]
         variant = VARIANT_LOCAL if Q is not None else VARIANT_GLOBAL
-        p = cls._params(2 * h, T, M, variant, 0)
+        p = cls._params(2 * h, T, M, variant, 0, opq=rotations is not None)
         qs = [np.ascontiguousarray(a, dtype=np.float32) if a is not None else None for a in (Q, S)]
         h_out = ctypes.c_void_p()
         _check(lib().bpq_create(ctypes.byref(h_out), ctypes.byref(p), C1.ctypes.data, C2.ctypes.data,
                                 R.ctypes.data, qs[0].ctypes.data if qs[0] is not None else None,
                                 qs[1].ctypes.data if qs[1] is not None else None, device))
-        return cls(h_out, device)
+        ix = cls(h_out, device)
+        if rotations is not None:
+            rs = [np.ascontiguousarray(r, dtype=np.float64) for r in rotations]
+            _check(lib().bpq_set_rotations(ix._h, rs[0].ctypes.data, rs[1].ctypes.data, rs[2].ctypes.data))
+        return ix
 
     @classmethod
-    def train(cls, learn, T, M, variant="global", iters=10, stream=None):
-        """Train codebooks on the GPU from an (n, D) float32 CUDA tensor of integer-valued vectors."""
+    def train(cls, learn, T, M, variant="global", iters=10, stream=None, opq=False):
+        """Train codebooks on the GPU from an (n, D) float32 CUDA tensor of integer-valued vectors
+        (opq: with OPQ rotations learned first)."""
         import torch
         assert learn.is_cuda and learn.dtype == torch.float32 and learn.is_contiguous()
         v = VARIANT_LOCAL if variant == "local" else VARIANT_GLOBAL
-        p = cls._params(learn.shape[1], T, M, v, iters)
+        p = cls._params(learn.shape[1], T, M, v, iters, opq=opq)
         h_out = ctypes.c_void_p()
         _check(lib().bpq_train_load(ctypes.byref(h_out), ctypes.byref(p), _ptr(learn), learn.shape[0], None,
                                     learn.device.index or 0, _stream(stream)))
@@ -381,6 +389,15 @@ class Index:
     def set_hbpq_table_budget(self, slots_per_query):
         """Table slots reserved per query by the HBPQ table form (0 = automatic)."""
         _check(lib().bpq_set_hbpq_table_budget(self._h, float(slots_per_query)))
+
+    def rotations(self):
+        """(R0, R1, R2) of an OPQ index as FP64 host arrays."""
+        p = self.params
+        R0 = np.empty((p.D, p.D))
+        R1 = np.empty((p.D // 2, p.D // 2))
+        R2 = np.empty((p.D // 2, p.D // 2))
+        _check(lib().bpq_get_rotations(self._h, R0.ctypes.data, R1.ctypes.data, R2.ctypes.data))
+        return R0, R1, R2
 
     def set_scan_work_size(self, candidates_per_item):
         """0: one CTA per query; W > 0: persistent work-queue scan with items of about W candidates."""

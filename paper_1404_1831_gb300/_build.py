@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 BPQ_SOURCES = ["bpq_api.cu", "bpq_tables.cu", "bpq_traverse.cu", "bpq_scan.cu", "bpq_build.cu", "bpq_noalloc.cu",
-               "bpq_hbpq.cu", "bpq_serve.cu", "bpq_graph.cu"]
+               "bpq_hbpq.cu", "bpq_serve.cu", "bpq_graph.cu",
+               "bpq_opq.cu"]
 
 
 def nvcc():

@@ -3,6 +3,7 @@
 //   tables (K1/K2) -> traversal (K4) -> scan + top-k (K5/K6)
 // enqueued on the caller's stream, chunk by chunk when the workspace is small.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -60,6 +61,8 @@ void check_params(const bpq_params* p) {
   BPQ_CHECK(p->T >= 1 && p->T <= MAX_T, BPQ_EINVAL, "T must be in [1, 4096]");
   BPQ_CHECK(p->variant == BPQ_VARIANT_GLOBAL || p->variant == BPQ_VARIANT_LOCAL, BPQ_EINVAL, "bad variant");
   BPQ_CHECK(p->kmeans_iters >= 0 && p->kmeans_iters <= 1000, BPQ_EINVAL, "kmeans_iters out of range");
+  BPQ_CHECK(p->opq == 0 || p->opq == 1, BPQ_EINVAL, "opq must be 0 or 1");
+  BPQ_CHECK(!p->opq || p->variant == BPQ_VARIANT_GLOBAL, BPQ_EINVAL, "OPQ rotations are built for the global codebooks");
   BPQ_CHECK(scan_supported(p->D, p->M), BPQ_EINVAL,
             "this build supports (D, M) in {(128, 8), (128, 16), (384, 8), (32, 8), (8, 8)}");
 }
@@ -115,6 +118,7 @@ struct Layout {
   size_t status, qcounter, L, d1, d2, lut, cells, ncells, npoints, total;
   size_t hb_qbase, hb_qrows, hb_qbits, hb_hmap, hb_ctr, hb_fb, hb_tab;
   size_t wq_ctr, wq_items, wq_merges, wq_pids, wq_pdists;  // work-queue scan
+  size_t rq_c, rq_r;  // OPQ: rot0 q and B rot0 q of the chunk's queries
   int64_t cap, hb_slots;
   bool wq;
 };
@@ -151,6 +155,12 @@ Layout layout(const bpq_index& ix, int64_t nq, int64_t L_max, int scorer, bool w
   o = align_up(o + (size_t)nq * 4);
   l.npoints = o;
   o = align_up(o + (size_t)nq * 8);
+  if (ix.opq) {
+    l.rq_c = o;
+    o = align_up(o + (size_t)nq * ix.p.D * 4);
+    l.rq_r = o;
+    o = align_up(o + (size_t)nq * ix.p.D * 4);
+  }
   if (with_cells && hbpq_tables_used(scorer, k)) {
     const int TW = (ix.p.T + 31) / 32;
     if (hb_per_query <= 0.0) hb_per_query = hbpq_slots_per_query(ix, (double)L_max);
@@ -224,8 +234,8 @@ ScanArgs scan_args(const bpq_index& ix, const float* q, int64_t nq, const float*
   sa.X2 = ix.X2.as<float>();
   sa.cross = ix.cross.as<float>();
   sa.queries = q;
-  sa.C1 = ix.C1.as<float>();
-  sa.C2 = ix.C2.as<float>();
+  sa.C1 = ix.opq ? ix.C1r.as<float>() : ix.C1.as<float>();  // the reconstruction's centroids
+  sa.C2 = ix.opq ? ix.C2r.as<float>() : ix.C2.as<float>();  // (residual space with OPQ)
   sa.R = ix.R.as<float>();
   sa.Q = ix.Q.as<float>();
   sa.S = ix.S.as<float>();
@@ -322,7 +332,18 @@ void bpq::run_queries(const bpq_index& ix, const float* q, int64_t nq, const int
     float* d1 = reinterpret_cast<float*>(w + l.d1);
     float* d2 = reinterpret_cast<float*>(w + l.d2);
     float* lut = (scan && uses_lut(scorer)) ? reinterpret_cast<float*>(w + l.lut) : nullptr;
-    launch_query_tables(ix, qc, nc, d1, d2, lut, st, reinterpret_cast<int32_t*>(w + l.status));
+    // OPQ: the coarse tables and the traversal use rot0 q, the PQ table and the
+    // reconstruction scorer B rot0 q (with the rotated centroids)
+    const float* qcoarse = qc;
+    const float* qres = qc;
+    if (ix.opq) {
+      float* rc = reinterpret_cast<float*>(w + l.rq_c);
+      float* rr = reinterpret_cast<float*>(w + l.rq_r);
+      rotate_for_index(ix, qc, nc, rc, rr, st);
+      qcoarse = rc;
+      qres = rr;
+    }
+    launch_query_tables(ix, qcoarse, nc, d1, d2, lut, st, reinterpret_cast<int32_t*>(w + l.status), qres);
     TraverseArgs ta{};
     ta.d1 = d1;
     ta.d2 = d2;
@@ -352,7 +373,7 @@ void bpq::run_queries(const bpq_index& ix, const float* q, int64_t nq, const int
     }
     launch_traverse(ta, st);
     if (!scan) continue;
-    ScanArgs sa = scan_args(ix, qc, nc, lut, ta.cells, ta.ncells, ta.cap, k, out_ids + c0 * k,
+    ScanArgs sa = scan_args(ix, qres, nc, lut, ta.cells, ta.ncells, ta.cap, k, out_ids + c0 * k,
                             out_dists + c0 * k, reinterpret_cast<int32_t*>(w + l.qcounter));
     if (hb) {
       // per-(query, visited half-cell) tables on the tensor cores, then the M-lookup scan
@@ -461,7 +482,16 @@ void run_shortlist(const bpq_index& ix, const float* q, int64_t nq, const int64_
     void* lutr = w + l.lutr;
     float* scale = reinterpret_cast<float*>(w + l.scale);
     uint64_t* sl = reinterpret_cast<uint64_t*>(w + l.sl);
-    launch_query_tables(ix, qc, nc, d1, d2, lut, st);
+    const float* qcoarse = qc;
+    const float* qres = qc;
+    if (ix.opq) {
+      float* rc = reinterpret_cast<float*>(w + l.base.rq_c);
+      float* rr = reinterpret_cast<float*>(w + l.base.rq_r);
+      rotate_for_index(ix, qc, nc, rc, rr, st);
+      qcoarse = rc;
+      qres = rr;
+    }
+    launch_query_tables(ix, qcoarse, nc, d1, d2, lut, st, nullptr, qres);
     launch_quant_lut(lut, ix.p.M, nc, lutr, scale, f16, st);
     TraverseArgs ta{};
     ta.d1 = d1;
@@ -543,6 +573,21 @@ void write_section(FILE* f, const void* dev, size_t bytes) {
             BPQ_EIO, "write failed");
 }
 
+void write_host_section(FILE* f, const void* data, size_t bytes) {
+  uint64_t n = bytes, h = fnv1a(data, bytes);
+  BPQ_CHECK(fwrite(&n, 8, 1, f) == 1 && (bytes == 0 || fwrite(data, 1, bytes, f) == bytes) && fwrite(&h, 8, 1, f) == 1,
+            BPQ_EIO, "write failed");
+}
+
+void read_host_section(FILE* f, std::vector<double>& dst, size_t count) {
+  uint64_t n = 0, h = 0;
+  BPQ_CHECK(fread(&n, 8, 1, f) == 1 && n == count * 8, BPQ_ECORRUPT, "index file section has the wrong size");
+  dst.resize(count);
+  BPQ_CHECK((count == 0 || fread(dst.data(), 8, count, f) == count) && fread(&h, 8, 1, f) == 1, BPQ_ECORRUPT,
+            "truncated index file");
+  BPQ_CHECK(h == fnv1a(dst.data(), count * 8), BPQ_ECORRUPT, "index file checksum mismatch");
+}
+
 void read_section(FILE* f, DevBuf& dst, size_t bytes) {
   uint64_t n = 0, h = 0;
   BPQ_CHECK(fread(&n, 8, 1, f) == 1, BPQ_ECORRUPT, "truncated index file");
@@ -564,8 +609,11 @@ bpq_index* load_file(const char* path, int device) {
   bpq_params p{};
   int64_t n = 0;
   BPQ_CHECK(fread(magic, 8, 1, fh.f) == 1 && memcmp(magic, MAGIC, 8) == 0, BPQ_ECORRUPT, "not a bpq index file");
-  BPQ_CHECK(fread(&version, 4, 1, fh.f) == 1 && version == 1, BPQ_ECORRUPT, "unsupported index file version");
-  BPQ_CHECK(fread(&p, sizeof(p), 1, fh.f) == 1 && fread(&n, 8, 1, fh.f) == 1, BPQ_ECORRUPT, "truncated header");
+  BPQ_CHECK(fread(&version, 4, 1, fh.f) == 1 && (version == 1 || version == 2), BPQ_ECORRUPT,
+            "unsupported index file version");
+  // version 1 files end the params before the opq field
+  const size_t psize = version == 1 ? offsetof(bpq_params, opq) : sizeof(p);
+  BPQ_CHECK(fread(&p, psize, 1, fh.f) == 1 && fread(&n, 8, 1, fh.f) == 1, BPQ_ECORRUPT, "truncated header");
   try {
     check_params(&p);
   } catch (const Error& e) {
@@ -582,6 +630,13 @@ bpq_index* load_file(const char* path, int device) {
     if (p.variant == BPQ_VARIANT_LOCAL) {
       read_section(fh.f, ix->Q, cb_floats_local(p) * 4);
       read_section(fh.f, ix->S, cb_floats_local(p) * 4);
+    }
+    if (p.opq) {
+      std::vector<double> r0, r1, r2;
+      read_host_section(fh.f, r0, (size_t)p.D * p.D);
+      read_host_section(fh.f, r1, (size_t)(p.D / 2) * (p.D / 2));
+      read_host_section(fh.f, r2, (size_t)(p.D / 2) * (p.D / 2));
+      set_opq_rotations(*ix, r0.data(), r1.data(), r2.data(), 0);
     }
     read_section(fh.f, ix->offsets, ((size_t)p.T * p.T + 1) * 4);
     read_section(fh.f, ix->codes, (size_t)n * p.M);
@@ -776,8 +831,19 @@ int bpq_query_tables(const bpq_index* ix, const float* q, int64_t nq, float* d1,
     const int64_t step = 65535LL * 64;
     for (int64_t c0 = 0; c0 < nq; c0 += step) {
       const int64_t nc = std::min(step, nq - c0);
-      launch_query_tables(*ix, q + c0 * ix->p.D, nc, d1 + c0 * ix->p.T, d2 + c0 * ix->p.T,
-                          lut ? lut + c0 * ix->p.M * KSUB : nullptr, st);
+      const float* qcoarse = q + c0 * ix->p.D;
+      const float* qres = qcoarse;
+      DevBuf rc, rr;
+      if (ix->opq) {  // rot0 q for the coarse tables, B rot0 q for the PQ table
+        rc.alloc((size_t)nc * ix->p.D * 4);
+        rr.alloc((size_t)nc * ix->p.D * 4);
+        rotate_for_index(*ix, qcoarse, nc, rc.as<float>(), rr.as<float>(), st);
+        qcoarse = rc.as<float>();
+        qres = rr.as<float>();
+      }
+      launch_query_tables(*ix, qcoarse, nc, d1 + c0 * ix->p.T, d2 + c0 * ix->p.T,
+                          lut ? lut + c0 * ix->p.M * KSUB : nullptr, st, nullptr, qres);
+      if (ix->opq) BPQ_CUDA(cudaStreamSynchronize(st));  // the rotated copies are released here
     }
   });
 }
@@ -846,8 +912,15 @@ int bpq_scan(const bpq_index* ix, const float* q, int64_t nq, const float* lut, 
     BPQ_CHECK(!uses_lut(scorer) || lut, BPQ_EINVAL, "FBPQ needs the query tables");
     BPQ_CHECK(uses_lut(scorer) || q, BPQ_EINVAL, "reconstruction needs the queries");
     DeviceGuard dg(ix->device);
-    launch_scan(scan_args(*ix, q, nq, lut, cells, ncells, cap, k, ids, dists, counter), scorer,
-                static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevBuf rr;
+    if (ix->opq && !uses_lut(scorer)) {  // the reconstruction scorer works in the residual space
+      rr.alloc((size_t)nq * ix->p.D * 4);
+      rotate_for_index(*ix, q, nq, nullptr, rr.as<float>(), st);
+      q = rr.as<float>();
+    }
+    launch_scan(scan_args(*ix, q, nq, lut, cells, ncells, cap, k, ids, dists, counter), scorer, st);
+    if (rr.p) BPQ_CUDA(cudaStreamSynchronize(st));
   });
 }
 
@@ -967,6 +1040,28 @@ int bpq_autotune(bpq_index* ix, const float* q, int64_t nq, const int64_t* L_hos
   });
 }
 
+int bpq_set_rotations(bpq_index* ix, const double* R0, const double* R1, const double* R2) {
+  return guard([&] {
+    BPQ_CHECK(ix && R0 && R1 && R2, BPQ_EINVAL, "NULL pointer");
+    BPQ_CHECK(ix->p.opq, BPQ_EINVAL, "the index was made without OPQ (params.opq = 0)");
+    BPQ_CHECK(ix->n_points == 0 && ix->n_pending == 0, BPQ_ESTATE, "rotations must be set before points are added");
+    DeviceGuard dg(ix->device);
+    set_opq_rotations(*ix, R0, R1, R2, 0);
+    build_fbpq_tables(*ix, 0);
+    BPQ_CUDA(cudaDeviceSynchronize());
+  });
+}
+
+int bpq_get_rotations(const bpq_index* ix, double* R0, double* R1, double* R2) {
+  return guard([&] {
+    BPQ_CHECK(ix && R0 && R1 && R2, BPQ_EINVAL, "NULL pointer");
+    BPQ_CHECK(ix->opq, BPQ_ESTATE, "the index has no rotations");
+    std::copy(ix->h_rot0.begin(), ix->h_rot0.end(), R0);
+    std::copy(ix->h_rot1.begin(), ix->h_rot1.end(), R1);
+    std::copy(ix->h_rot2.begin(), ix->h_rot2.end(), R2);
+  });
+}
+
 int bpq_set_scan_work_size(bpq_index* ix, int32_t candidates_per_item) {
   return guard([&] {
     BPQ_CHECK(ix, BPQ_EINVAL, "index is NULL");
@@ -987,7 +1082,8 @@ int bpq_get_info(const bpq_index* ix, bpq_info* out) {
                                   ix->ids.bytes + ix->cross.bytes + ix->pend_cells.bytes + ix->pend_codes.bytes +
                                   ix->pend_ids.bytes + ix->C1b.bytes + ix->C2b.bytes + ix->Rb.bytes + ix->n1.bytes +
                                   ix->n2.bytes + ix->nR.bytes + ix->Qb.bytes + ix->Sb.bytes + ix->E1.bytes +
-                                  ix->E2.bytes);
+                                  ix->E2.bytes + ix->rot0t.bytes + ix->rotBt.bytes + ix->rotPt.bytes +
+                                  ix->C1r.bytes + ix->C2r.bytes);
     out->params = ix->p;
   });
 }
@@ -1018,7 +1114,7 @@ int bpq_save(const bpq_index* ix, const char* path) {
     File fh;
     fh.f = fopen(path, "wb");
     BPQ_CHECK(fh.f, BPQ_EIO, std::string("cannot open ") + path + " for writing");
-    const uint32_t version = 1;
+    const uint32_t version = 2;
     const int64_t n = ix->n_points;
     BPQ_CHECK(fwrite(MAGIC, 8, 1, fh.f) == 1 && fwrite(&version, 4, 1, fh.f) == 1 &&
                   fwrite(&ix->p, sizeof(ix->p), 1, fh.f) == 1 && fwrite(&n, 8, 1, fh.f) == 1,
@@ -1029,6 +1125,12 @@ int bpq_save(const bpq_index* ix, const char* path) {
     if (ix->p.variant == BPQ_VARIANT_LOCAL) {
       write_section(fh.f, ix->Q.p, ix->Q.bytes);
       write_section(fh.f, ix->S.p, ix->S.bytes);
+    }
+    if (ix->p.opq) {
+      BPQ_CHECK(ix->opq, BPQ_ESTATE, "an OPQ index needs its rotations (bpq_set_rotations) before it is saved");
+      write_host_section(fh.f, ix->h_rot0.data(), ix->h_rot0.size() * 8);
+      write_host_section(fh.f, ix->h_rot1.data(), ix->h_rot1.size() * 8);
+      write_host_section(fh.f, ix->h_rot2.data(), ix->h_rot2.size() * 8);
     }
     write_section(fh.f, ix->offsets.p, ((size_t)ix->p.T * ix->p.T + 1) * 4);
     write_section(fh.f, ix->codes.p, (size_t)n * ix->p.M);

@@ -116,14 +116,20 @@ __global__ void displacement_kernel(const float* __restrict__ X, int64_t n, cons
 }
 
 // Encoding of Eqs. 6-7 (global codebooks) or Eq. 12 (local codebooks).
+// With OPQ, X holds rot0 x (cells) and XR the residual-space vectors B rot0 x, with
+// C1r, C2r the rotated centroids B c (the code is of XR - C1r/C2r); otherwise
+// XR = X and C1r, C2r = C1, C2.
 template <int H, int SUB>
 __global__ void encode_kernel(const float* __restrict__ X, int64_t n, const float* __restrict__ C1,
                               const float* __restrict__ C2, int T, const float* __restrict__ R,
                               const float* __restrict__ Q, const float* __restrict__ S, int M,
-                              int32_t* __restrict__ cell_out, uint8_t* __restrict__ codes_out) {
+                              int32_t* __restrict__ cell_out, uint8_t* __restrict__ codes_out,
+                              const float* __restrict__ XR, const float* __restrict__ C1r,
+                              const float* __restrict__ C2r) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const float* xp = X + p * 2 * H;
+  const float* xrp = XR + p * 2 * H;
   float x[H];
 #pragma unroll
   for (int t = 0; t < H; ++t) x[t] = xp[t];
@@ -136,10 +142,10 @@ __global__ void encode_kernel(const float* __restrict__ X, int64_t n, const floa
   for (int k = 0; k < M; ++k) {
     const bool second = k >= m2;
     const int kk = second ? k - m2 : k;
-    const float* cen = second ? C2 + (int64_t)j * H + kk * SUB : C1 + (int64_t)i * H + kk * SUB;
+    const float* cen = second ? C2r + (int64_t)j * H + kk * SUB : C1r + (int64_t)i * H + kk * SUB;
     float r[SUB];
 #pragma unroll
-    for (int t = 0; t < SUB; ++t) r[t] = xp[k * SUB + t] - cen[t];
+    for (int t = 0; t < SUB; ++t) r[t] = xrp[k * SUB + t] - cen[t];
     const float* cb;
     if (Q)
       cb = second ? S + ((int64_t)j * m2 + kk) * KSUB * SUB : Q + ((int64_t)i * m2 + kk) * KSUB * SUB;
@@ -460,10 +466,23 @@ void displacement(const float* X, int64_t n, const bpq_index& ix, float* disp, i
 template <int H, int SUB>
 void encode_t(const bpq_index& ix, const float* x, int64_t n, int32_t* cell, uint8_t* codes, cudaStream_t st) {
   const bool local = ix.p.variant == BPQ_VARIANT_LOCAL;
+  const float* xc = x;
+  const float* xr = x;
+  DevBuf bc, br;
+  if (ix.opq) {  // rot0 x for the cell, B rot0 x for the code
+    bc.alloc((size_t)n * ix.p.D * 4);
+    br.alloc((size_t)n * ix.p.D * 4);
+    rotate_for_index(ix, x, n, bc.as<float>(), br.as<float>(), st);
+    xc = bc.as<float>();
+    xr = br.as<float>();
+  }
+  const float* c1r = ix.opq ? ix.C1r.as<float>() : ix.C1.as<float>();
+  const float* c2r = ix.opq ? ix.C2r.as<float>() : ix.C2.as<float>();
   encode_kernel<H, SUB><<<blocks_for(n, 128), 128, 0, st>>>(
-      x, n, ix.C1.as<float>(), ix.C2.as<float>(), ix.p.T, ix.R.as<float>(), local ? ix.Q.as<float>() : nullptr,
-      local ? ix.S.as<float>() : nullptr, ix.p.M, cell, codes);
+      xc, n, ix.C1.as<float>(), ix.C2.as<float>(), ix.p.T, ix.R.as<float>(), local ? ix.Q.as<float>() : nullptr,
+      local ? ix.S.as<float>() : nullptr, ix.p.M, cell, codes, xr, c1r, c2r);
   check_launch("encode");
+  if (ix.opq) BPQ_CUDA(cudaStreamSynchronize(st));  // the rotated copies are released here
 }
 
 }  // namespace
@@ -484,10 +503,18 @@ void launch_reconstruction_error(const bpq_index& ix, const float* x, int64_t n,
   if (n <= 0) return;
   const bool local = ix.p.variant == BPQ_VARIANT_LOCAL;
   const int64_t threads = n * 32;
+  DevBuf xr;
+  if (ix.opq) {  // ||x - xhat|| = ||B rot0 x - (B c + r)|| (orthogonal rotations)
+    xr.alloc((size_t)n * ix.p.D * 4);
+    rotate_for_index(ix, x, n, nullptr, xr.as<float>(), st);
+    x = xr.as<float>();
+  }
   recon_error_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-      x, n, cells, codes, ix.C1.as<float>(), ix.C2.as<float>(), ix.p.T, ix.p.D, ix.p.M, ix.R.as<float>(),
+      x, n, cells, codes, ix.opq ? ix.C1r.as<float>() : ix.C1.as<float>(),
+      ix.opq ? ix.C2r.as<float>() : ix.C2.as<float>(), ix.p.T, ix.p.D, ix.p.M, ix.R.as<float>(),
       local ? ix.Q.as<float>() : nullptr, local ? ix.S.as<float>() : nullptr, err);
   check_launch("reconstruction error kernel");
+  if (ix.opq) BPQ_CUDA(cudaStreamSynchronize(st));
 }
 
 void fill_sequential_ids(int32_t* ids, int64_t n, int64_t start, cudaStream_t st) {
@@ -599,6 +626,23 @@ void train_codebooks(bpq_index& ix, const float* learn, int64_t n, cudaStream_t 
     BPQ_CUDA(cudaStreamSynchronize(st));
     BPQ_CHECK(!bad, BPQ_EINVAL, "learn vectors must be integer-valued with |x| <= 2^20");
   }
+  DevBuf learn_rot;
+  std::vector<double> R0;
+  if (ix.p.opq) {  // rot0 of the learn set (two subspaces), applied and rounded to the integer grid
+    R0 = opq_learn_rotation(learn, n, D, 0, D, 2, st);
+    DevBuf r0t;
+    {
+      std::vector<double> t((size_t)D * D);
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) t[(size_t)j * D + i] = R0[(size_t)i * D + j];
+      r0t.alloc(t.size() * 8);
+      BPQ_CUDA(cudaMemcpy(r0t.p, t.data(), t.size() * 8, cudaMemcpyHostToDevice));
+    }
+    learn_rot.alloc((size_t)n * D * 4);
+    rotate_rows(learn, n, D, r0t.as<double>(), 1, true, learn_rot.as<float>(), st);
+    BPQ_CUDA(cudaStreamSynchronize(st));
+    learn = learn_rot.as<float>();
+  }
   // coarse codebooks C^1, C^2: K-means on the halves, starting from the first T vectors
   ix.C1.alloc((size_t)T * h * 4);
   ix.C2.alloc((size_t)T * h * 4);
@@ -616,6 +660,25 @@ void train_codebooks(bpq_index& ix, const float* learn, int64_t n, cudaStream_t 
   else if (h == 16) displacement<16>(learn, n, ix, disp.as<float>(), gi.as<int32_t>(), gj.as<int32_t>(), st);
   else if (h == 4) displacement<4>(learn, n, ix, disp.as<float>(), gi.as<int32_t>(), gj.as<int32_t>(), st);
   else throw Error(BPQ_EINVAL, "unsupported D for training");
+  std::vector<double> R1, R2;
+  if (ix.p.opq) {  // rot1, rot2 of the displacement halves (M/2 subspaces each), applied and rounded
+    R1 = opq_learn_rotation(disp.as<float>(), n, D, 0, h, m2, st);
+    R2 = opq_learn_rotation(disp.as<float>(), n, D, h, h, m2, st);
+    DevBuf bt;
+    {
+      std::vector<double> t((size_t)2 * h * h);
+      for (int b = 0; b < 2; ++b)
+        for (int i = 0; i < h; ++i)
+          for (int j = 0; j < h; ++j) t[(size_t)b * h * h + (size_t)j * h + i] = (b ? R2 : R1)[(size_t)i * h + j];
+      bt.alloc(t.size() * 8);
+      BPQ_CUDA(cudaMemcpy(bt.p, t.data(), t.size() * 8, cudaMemcpyHostToDevice));
+    }
+    DevBuf dr;
+    dr.alloc((size_t)n * D * 4);
+    rotate_rows(disp.as<float>(), n, D, bt.as<double>(), 2, true, dr.as<float>(), st);
+    BPQ_CUDA(cudaMemcpyAsync(disp.p, dr.p, (size_t)n * D * 4, cudaMemcpyDeviceToDevice, st));
+    BPQ_CUDA(cudaStreamSynchronize(st));
+  }
   ix.R.alloc((size_t)M * KSUB * s * 4);
   for (int k = 0; k < M; ++k) {
     float* Rk = ix.R.as<float>() + (size_t)k * KSUB * s;
@@ -645,6 +708,7 @@ void train_codebooks(bpq_index& ix, const float* learn, int64_t n, cudaStream_t 
       }
     }
   }
+  if (ix.p.opq) set_opq_rotations(ix, R0.data(), R1.data(), R2.data(), st);
   BPQ_CUDA(cudaStreamSynchronize(st));
 }
 

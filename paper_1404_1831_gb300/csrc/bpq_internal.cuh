@@ -8,6 +8,7 @@
 #include <map>
 #include <stdexcept>
 #include <string>
+#include <vector>
 
 #include "../../include/bpq.h"
 
@@ -219,6 +220,11 @@ struct bpq_index {
   bpq::DevBuf Qb, Sb, E1, E2;
   bool local_bf16_exact = false;
   double hb_slots_per_query = 0.0;  // 0: automatic (bpq_set_hbpq_table_budget)
+  // OPQ: rotations (host FP64 copies; device FP64 transposed blocks for rotate_rows:
+  // rot0, B = blockdiag(rot1, rot2), P = B rot0) and the rotated coarse centroids B c
+  bool opq = false;
+  std::vector<double> h_rot0, h_rot1, h_rot2;
+  bpq::DevBuf rot0t, rotBt, rotPt, C1r, C2r;
   int32_t scan_work_W = 0;          // candidates per work item of the scan; 0: one CTA per query
   // work-item sizes chosen by bpq_autotune, per batch class (scorer, k <= 32, log2 nq,
   // log2 mean L); a class found here overrides scan_work_W
@@ -237,8 +243,9 @@ namespace bpq {
 // Query tables (bpq_tables.cu).
 // status: workspace status word (may be NULL); a tensor-core tile whose bounded
 // wait gave up sets STATUS_TIMEOUT there and is recomputed on the CUDA cores.
+// q_lut: the queries for the PQ table when they differ from q (OPQ: q~ = B rot0 q, q = rot0 q)
 void launch_query_tables(const bpq_index& ix, const float* q, int64_t nq, float* d1, float* d2,
-                         float* lut, cudaStream_t st, int32_t* status = nullptr);
+                         float* lut, cudaStream_t st, int32_t* status = nullptr, const float* q_lut = nullptr);
 void build_fbpq_tables(bpq_index& ix, cudaStream_t st);
 
 // Bits of the workspace status word.
@@ -381,6 +388,15 @@ void run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t*
                  int k, int scorer, int32_t* out_ids, float* out_dists, bpq_cell* user_cells, int32_t user_cap,
                  int32_t* user_ncells, int64_t* user_npoints, void* ws, size_t ws_bytes, cudaStream_t st,
                  const int32_t* L32_pinned = nullptr);
+
+// OPQ (bpq_opq.cu).  rotate_rows: Y = R X per row within nblk diagonal blocks (Rt:
+// the blocks transposed, FP64), FP64 accumulation, rounded half up or FP32.
+void rotate_rows(const float* X, int64_t n, int D, const double* Rt, int nblk, bool round, float* Y, cudaStream_t st);
+void set_opq_rotations(bpq_index& ix, const double* R0, const double* R1, const double* R2, cudaStream_t st);
+// xc = rot0 x (coarse space), xr = B rot0 x (residual space); either may be NULL
+void rotate_for_index(const bpq_index& ix, const float* x, int64_t n, float* xc, float* xr, cudaStream_t st);
+std::vector<double> opq_learn_rotation(const float* X, int64_t n, int64_t ld, int col, int d, int groups,
+                                       cudaStream_t st);
 
 // Index build (bpq_build.cu).
 void launch_encode(const bpq_index& ix, const float* x, int64_t n, int32_t* cell, uint8_t* codes,

@@ -308,7 +308,8 @@ void launch_quant_lut(const float* lut, int M, int64_t nq, void* out, float* sca
 }
 
 void launch_query_tables(const bpq_index& ix, const float* q, int64_t nq, float* d1, float* d2,
-                         float* lut, cudaStream_t st, int32_t* status) {
+                         float* lut, cudaStream_t st, int32_t* status, const float* q_lut) {
+  if (!q_lut) q_lut = q;
   if (nq <= 0) return;
   const int D = ix.p.D, T = ix.p.T, M = ix.p.M;
   const int ty = (int)((nq + TC_M - 1) / TC_M);
@@ -339,7 +340,7 @@ void launch_query_tables(const bpq_index& ix, const float* q, int64_t nq, float*
     const size_t smem = (size_t)(TC_M + TC_N) * ix.ks * 2;
     BPQ_CUDA(cudaFuncSetAttribute(tc_table_kernel<MODE_LUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(1, ty, M);
-    tc_table_kernel<MODE_LUT><<<grid, 128, smem, st>>>(q, D, (int)nq, pp, status);
+    tc_table_kernel<MODE_LUT><<<grid, 128, smem, st>>>(q_lut, D, (int)nq, pp, status);
     check_launch("pq table kernel");
   }
 }
@@ -350,10 +351,11 @@ void build_fbpq_tables(bpq_index& ix, cudaStream_t st) {
   ix.X1.alloc(n * sizeof(float));
   ix.X2.alloc(n * sizeof(float));
   const int blocks = (int)((n + 255) / 256);
-  cross_table_kernel<<<blocks, 256, 0, st>>>(ix.C1.as<float>(), ix.R.as<float>(), T, ix.m2, ix.s, ix.h,
-                                             0, ix.X1.as<float>());
-  cross_table_kernel<<<blocks, 256, 0, st>>>(ix.C2.as<float>(), ix.R.as<float>(), T, ix.m2, ix.s, ix.h,
-                                             ix.m2, ix.X2.as<float>());
+  // with OPQ the dot products of Eq. 9 are in the residual space: rotated centroids B c
+  const float* c1 = ix.opq ? ix.C1r.as<float>() : ix.C1.as<float>();
+  const float* c2 = ix.opq ? ix.C2r.as<float>() : ix.C2.as<float>();
+  cross_table_kernel<<<blocks, 256, 0, st>>>(c1, ix.R.as<float>(), T, ix.m2, ix.s, ix.h, 0, ix.X1.as<float>());
+  cross_table_kernel<<<blocks, 256, 0, st>>>(c2, ix.R.as<float>(), T, ix.m2, ix.s, ix.h, ix.m2, ix.X2.as<float>());
   check_launch("fbpq cross table kernel");
   // tensor-core operands of the query tables
   ix.kh = (ix.h + 15) & ~15;

@@ -34,7 +34,11 @@ def test_library_exports_every_declared_symbol(so):
 
 def test_struct_layouts_match_header():
     hdr = open(os.path.join(ROOT, "include", "bpq.h")).read()
-    assert ctypes.sizeof(bpq.Params) == 6 * 4
+    params = re.search(r"typedef struct \{([^{}]*)\} bpq_params;", hdr, re.S).group(1)
+    fields = re.findall(r"int32_t (\w+);", params)
+    assert [f for f, _ in bpq.Params._fields_] == fields and ctypes.sizeof(bpq.Params) == 4 * len(fields)
+    cfg = re.search(r"typedef struct \{([^{}]*)\} bpq_server_config;", hdr, re.S).group(1)
+    assert [f for f, _ in bpq.ServerConfig._fields_] == re.findall(r"(?:int32_t|int64_t|size_t) (\w+);", cfg)
     assert bpq.CELL_DTYPE.itemsize == 16
     assert re.search(r"uint32_t cell;.*uint32_t begin;.*uint32_t count;.*float key;", hdr, re.S)
 
