@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the Poisson serving measurement")
     ap.add_argument("--no-configs", action="store_true", help="skip the 100M / 1B configuration blocks")
-    ap.add_argument("--workload", choices=("sift10m", "c3", "c4", "c5", "gist"), default="sift10m",
+    ap.add_argument("--workload", choices=("sift10m", "c3", "c4", "c5", "gist", "opq"), default="sift10m",
                     help="c3: 100M, M=16, int8 shortlist; c4: 100M, local codebooks, uneven L; "
                          "c5: 1B points, serving (each prints its own JSON line)")
     ap.add_argument("--serve-seconds", type=float, default=0.25, help="arrival window per offered load")
@@ -484,7 +484,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_configs:
         # the 100M and 1B configurations, each on a fresh index (outside the timed region)
         out["configs"] = {}
-        for name in ("c3", "c4", "c5", "gist"):
+        for name in ("c3", "c4", "c5", "gist", "opq"):
             t0 = time.time()
             out["configs"][name] = config_block(name, args.serve_seconds)
             out["configs"][name]["wall_s"] = round(time.time() - t0, 1)
@@ -655,13 +655,13 @@ def config_block(name, serve_seconds=0.25):
     from synthdata import device as sdev
     dev = torch.device("cuda", 0)
     torch.backends.cuda.matmul.allow_tf32 = False
-    w = {"c3": sd.SIFT100M_M16, "c4": sd.SIFT100M, "c5": sd.SIFT1B, "gist": sd.GIST50M}[name]
+    w = {"c3": sd.SIFT100M_M16, "c4": sd.SIFT100M, "c5": sd.SIFT1B, "gist": sd.GIST50M, "opq": sd.SIFT10M}[name]
     mix = sd.make_mixture(w.seed, w.n_comp, w.dim)
     learn = sdev.points_cuda(mix, sd.STREAM_LEARN, 0, w.n_learn, device=dev)
 
-    def build(variant):
+    def build(variant, opq=False):
         t0 = time.time()
-        ix = bpq.Index.train(learn, w.T, w.M, variant=variant, iters=w.kmeans_iters)
+        ix = bpq.Index.train(learn, w.T, w.M, variant=variant, iters=w.kmeans_iters, opq=opq)
         for s in range(0, w.n_base, 4_000_000):
             ix.add(sdev.points_cuda(mix, sd.STREAM_BASE, s, min(4_000_000, w.n_base - s), device=dev))
         ix.finalize()
@@ -751,6 +751,20 @@ def config_block(name, serve_seconds=0.25):
         out["hbpq_over_fbpq_time"] = out["hbpq"]["ms"] / out["fbpq"]["ms"]
         out["batching_fbpq"] = batching_block(ixg, q, Ls, k, "fbpq", reps=10)
         out["index_global"] = {"device_bytes": int(ixg.info().device_bytes)}
+    elif name == "opq":
+        # OMulti-D-OADC (the OPQ variant of the paper's experiments) next to the plain index
+        ixp, _ = build("global")
+        ixo, out["build_opq_s"] = build("global", opq=True)
+        del learn
+        out["encoding_error"] = {"plain": enc_error(ixp), "opq": enc_error(ixo), "points": "first 10M base points"}
+        for L in w.L:
+            row = {}
+            for tag, ixx in (("plain", ixp), ("opq", ixo)):
+                ms = timed(lambda: ixx.search(q, L, k, "fbpq"), reps=3, warm=2)
+                ids, _ = ixx.search(q[:1000], L, k, "fbpq")
+                row[tag] = {"qps": nq / (ms / 1e3), "ms": ms, "recall": recall_of(ids, nn)}
+            out[f"L{L}"] = row
+        out["index"] = {"device_bytes_opq": int(ixo.info().device_bytes)}
     elif name == "gist":
         # the paper's GIST50M rows (Table FBPQ): FBPQ vs reconstruction at D = 384, 8-byte codes
         ix, out["build_s"] = build("global")

@@ -339,7 +339,7 @@ void bpq::run_queries(const bpq_index& ix, const float* q, int64_t nq, const int
     if (ix.opq) {
       float* rc = reinterpret_cast<float*>(w + l.rq_c);
       float* rr = reinterpret_cast<float*>(w + l.rq_r);
-      rotate_for_index(ix, qc, nc, rc, rr, st);
+      rotate_queries(ix, qc, nc, rc, rr, st);
       qcoarse = rc;
       qres = rr;
     }
@@ -487,7 +487,7 @@ void run_shortlist(const bpq_index& ix, const float* q, int64_t nq, const int64_
     if (ix.opq) {
       float* rc = reinterpret_cast<float*>(w + l.base.rq_c);
       float* rr = reinterpret_cast<float*>(w + l.base.rq_r);
-      rotate_for_index(ix, qc, nc, rc, rr, st);
+      rotate_queries(ix, qc, nc, rc, rr, st);
       qcoarse = rc;
       qres = rr;
     }
@@ -837,7 +837,7 @@ int bpq_query_tables(const bpq_index* ix, const float* q, int64_t nq, float* d1,
       if (ix->opq) {  // rot0 q for the coarse tables, B rot0 q for the PQ table
         rc.alloc((size_t)nc * ix->p.D * 4);
         rr.alloc((size_t)nc * ix->p.D * 4);
-        rotate_for_index(*ix, qcoarse, nc, rc.as<float>(), rr.as<float>(), st);
+        rotate_queries(*ix, qcoarse, nc, rc.as<float>(), rr.as<float>(), st);
         qcoarse = rc.as<float>();
         qres = rr.as<float>();
       }
@@ -1083,7 +1083,7 @@ int bpq_get_info(const bpq_index* ix, bpq_info* out) {
                                   ix->pend_ids.bytes + ix->C1b.bytes + ix->C2b.bytes + ix->Rb.bytes + ix->n1.bytes +
                                   ix->n2.bytes + ix->nR.bytes + ix->Qb.bytes + ix->Sb.bytes + ix->E1.bytes +
                                   ix->E2.bytes + ix->rot0t.bytes + ix->rotBt.bytes + ix->rotPt.bytes +
-                                  ix->C1r.bytes + ix->C2r.bytes);
+                                  ix->C1r.bytes + ix->C2r.bytes + ix->rot0tf.bytes + ix->rotPtf.bytes);
     out->params = ix->p;
   });
 }

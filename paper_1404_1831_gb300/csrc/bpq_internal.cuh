@@ -213,6 +213,10 @@ struct bpq_index {
   bpq::DevBuf C1b, C2b, Rb, n1, n2, nR;
   int kh = 0, ks = 0;
   bool coarse_bf16_exact = false, R_bf16_exact = false;
+  // second BF16 planes v - bf16(v) (codewords of magnitude up to 2^16 are exact as
+  // the sum of two planes, e.g. integer codebooks in OPQ-rotated spaces)
+  bpq::DevBuf C1b2, C2b2, Rb2;
+  bool coarse_bf16x2_exact = false, R_bf16x2_exact = false;
   // HBPQ table form (local variant): BF16 copies of the local codebooks Q, S
   // (T x M/2 x 256 x ks, K padded with zeros) and the query-independent part of
   // the per-half-cell tables, E1[i][k][t] = ||Q^i_k[t]||^2 + 2<c^1_i|k, Q^i_k[t]>
@@ -225,6 +229,7 @@ struct bpq_index {
   bool opq = false;
   std::vector<double> h_rot0, h_rot1, h_rot2;
   bpq::DevBuf rot0t, rotBt, rotPt, C1r, C2r;
+  bpq::DevBuf rot0tf, rotPtf;  // FP32 transposed rot0 and P for the query rotation
   int32_t scan_work_W = 0;          // candidates per work item of the scan; 0: one CTA per query
   // work-item sizes chosen by bpq_autotune, per batch class (scorer, k <= 32, log2 nq,
   // log2 mean L); a class found here overrides scan_work_W
@@ -395,6 +400,8 @@ void rotate_rows(const float* X, int64_t n, int D, const double* Rt, int nblk, b
 void set_opq_rotations(bpq_index& ix, const double* R0, const double* R1, const double* R2, cudaStream_t st);
 // xc = rot0 x (coarse space), xr = B rot0 x (residual space); either may be NULL
 void rotate_for_index(const bpq_index& ix, const float* x, int64_t n, float* xc, float* xr, cudaStream_t st);
+// queries: qc = rot0 q, qr = B rot0 q in FP32 (both required)
+void rotate_queries(const bpq_index& ix, const float* q, int64_t n, float* qc, float* qr, cudaStream_t st);
 std::vector<double> opq_learn_rotation(const float* X, int64_t n, int64_t ld, int col, int d, int groups,
                                        cudaStream_t st);
 

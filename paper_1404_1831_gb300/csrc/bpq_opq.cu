@@ -214,6 +214,18 @@ void set_opq_rotations(bpq_index& ix, const double* R0, const double* R1, const 
     }
   }
   upload_transposed(ix.rotPt, {P.data()}, D);
+  {  // FP32 copies (transposed) of rot0 and P for the queries
+    std::vector<float> a((size_t)D * D), b((size_t)D * D);
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) {
+        a[(size_t)j * D + i] = (float)R0[(size_t)i * D + j];
+        b[(size_t)j * D + i] = (float)P[(size_t)i * D + j];
+      }
+    ix.rot0tf.alloc(a.size() * 4);
+    ix.rotPtf.alloc(b.size() * 4);
+    BPQ_CUDA(cudaMemcpy(ix.rot0tf.p, a.data(), a.size() * 4, cudaMemcpyHostToDevice));
+    BPQ_CUDA(cudaMemcpy(ix.rotPtf.p, b.data(), b.size() * 4, cudaMemcpyHostToDevice));
+  }
   // rotated coarse centroids B c (T x h per half) for the cross terms and the reconstruction scorer
   ix.C1r.alloc((size_t)T * h * 4);
   ix.C2r.alloc((size_t)T * h * 4);
@@ -229,6 +241,37 @@ void set_opq_rotations(bpq_index& ix, const double* R0, const double* R1, const 
 void rotate_for_index(const bpq_index& ix, const float* x, int64_t n, float* xc, float* xr, cudaStream_t st) {
   if (xc) rotate_rows(x, n, ix.p.D, ix.rot0t.as<double>(), 1, false, xc, st);
   if (xr) rotate_rows(x, n, ix.p.D, ix.rotPt.as<double>(), 1, false, xr, st);
+}
+
+namespace {
+// Queries: both rotations at once in FP32 (a query's D floats staged in shared
+// memory, one thread per output); rot0 and P = B rot0 as FP32 transposed copies.
+__global__ void rotate_queries_kernel(const float* __restrict__ X, int64_t n, int D, const float* __restrict__ R0t,
+                                      const float* __restrict__ Pt, float* __restrict__ yc, float* __restrict__ yr) {
+  extern __shared__ float xs[];
+  const int64_t p = blockIdx.x;
+  if (p >= n) return;
+  for (int j = threadIdx.x; j < D; j += blockDim.x) xs[j] = X[p * D + j];
+  __syncthreads();
+  for (int i = threadIdx.x; i < D; i += blockDim.x) {
+    float a = 0.f, b = 0.f;
+    for (int j = 0; j < D; ++j) {
+      a = fmaf(R0t[(int64_t)j * D + i], xs[j], a);
+      b = fmaf(Pt[(int64_t)j * D + i], xs[j], b);
+    }
+    yc[p * D + i] = a;
+    yr[p * D + i] = b;
+  }
+}
+}  // namespace
+
+void rotate_queries(const bpq_index& ix, const float* q, int64_t n, float* qc, float* qr, cudaStream_t st) {
+  if (n <= 0) return;
+  BPQ_CHECK(n < (1LL << 31), BPQ_EINVAL, "too many queries for the rotation kernel");
+  const int D = ix.p.D;
+  rotate_queries_kernel<<<(unsigned)n, 128, (size_t)D * 4, st>>>(q, n, D, ix.rot0tf.as<float>(),
+                                                                 ix.rotPtf.as<float>(), qc, qr);
+  check_launch("query rotation kernel");
 }
 
 std::vector<double> opq_learn_rotation(const float* X, int64_t n, int64_t ld, int col, int d, int groups,

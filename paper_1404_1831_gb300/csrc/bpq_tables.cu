@@ -33,9 +33,14 @@ enum { MODE_SQ = 0, MODE_LUT = 1 };
 // (BF16 copies made at index build), then out = ||a||^2 + ||b||^2 - 2 D (coarse
 // tables) or ||b||^2 - 2 D (PQ table).  Integer inputs of magnitude <= 256 are
 // exact in BF16, every product is below 2^16 and every partial sum below 2^24,
-// so the FP32 accumulation and the epilogue are exact.  A tile whose operands
-// are not all exact in BF16 is computed in FP32 on the CUDA cores instead, so the
-// tables never lose precision.
+// so the FP32 accumulation and the epilogue are exact.  Real-valued queries (OPQ
+// rotations) against exact codewords are split into three BF16 planes
+// a = a_hi + a_mid + a_lo (a_mid, a_lo the BF16 roundings of what is left), which
+// carry a's 24-bit mantissa; the three products with the same codewords are exact
+// and accumulate into one FP32 result, as accurate as an FP32 dot product (`split`,
+// when the launch gives the planes' shared memory).  Any other tile whose operands
+// BF16 cannot hold is computed in FP32 on the CUDA cores, so the tables never lose
+// precision.
 // Operands are K-major in shared memory without swizzle: 8-row x 16-byte core
 // matrices, core (row group g, column group c) at byte 128 (g * KB + c).
 // ---------------------------------------------------------------------------
@@ -46,7 +51,9 @@ struct TcProblem {
   const float* B;           // nb x dim FP32
   const float* bn;          // nb squared norms
   float* out;               // out[a * ldo + o_off + b]
-  int a_off, nb, dim, kpad, ldo, o_off, b_exact;
+  int a_off, nb, dim, kpad, ldo, o_off;
+  int b_planes;             // BF16 planes that hold B exactly: 1, 2 (Bb + Bb2), or 0 (none: CUDA cores)
+  const __nv_bfloat16* Bb2; // second plane B - bf16(B) (b_planes == 2)
 };
 struct TcProblems {
   TcProblem p[MAXP];
@@ -54,7 +61,7 @@ struct TcProblems {
 
 template <int MODE>
 __global__ void __launch_bounds__(128) tc_table_kernel(const float* __restrict__ A, int lda, int na,
-                                                       TcProblems probs, int32_t* status) {
+                                                       TcProblems probs, int32_t* status, int split, int bsplit) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
@@ -68,40 +75,46 @@ __global__ void __launch_bounds__(128) tc_table_kernel(const float* __restrict__
   const int kpad = pr.kpad, KB = kpad >> 3;
   unsigned char* sA = tsm;
   unsigned char* sB = tsm + TC_M * kpad * 2;
+  unsigned char* sA2 = sB + TC_N * kpad * 2;  // split planes of A (when `split`)
+  unsigned char* sA3 = sA2 + TC_M * kpad * 2;
+  unsigned char* sB2 = split ? sA3 + TC_M * kpad * 2 : sA2;  // second plane of B (when `bsplit`)
   int bad = 0;
-  if (((pr.dim | lda | pr.a_off) & 3) == 0) {  // query slices as float4 groups (kpad is a multiple of 16)
-    const int q4 = kpad >> 2;
-    for (int e = tid; e < TC_M * q4; e += 128) {
-      const int r = e / q4, k = (e - r * q4) << 2;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (a0 + r < na && k < pr.dim) v = *reinterpret_cast<const float4*>(A + (int64_t)(a0 + r) * lda + pr.a_off + k);
-      const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
-      bad |= __low2float(lo) != v.x || __high2float(lo) != v.y || __low2float(hi) != v.z || __high2float(hi) != v.w;
-      uint2 pk;
-      pk.x = *reinterpret_cast<const uint32_t*>(&lo);
-      pk.y = *reinterpret_cast<const uint32_t*>(&hi);
-      *reinterpret_cast<uint2*>(sA + core_off(r, k, KB)) = pk;
-    }
-  } else {
-    for (int e = tid; e < TC_M * kpad; e += 128) {
-      const int r = e / kpad, k = e - r * kpad;
-      const float v = (a0 + r < na && k < pr.dim) ? A[(int64_t)(a0 + r) * lda + pr.a_off + k] : 0.f;
-      const __nv_bfloat16 b = __float2bfloat16_rn(v);
-      bad |= __bfloat162float(b) != v;
-      *reinterpret_cast<__nv_bfloat16*>(sA + core_off(r, k, KB)) = b;
+  for (int e = tid; e < TC_M * kpad; e += 128) {
+    const int r = e / kpad, k = e - r * kpad;
+    const float v = (a0 + r < na && k < pr.dim) ? A[(int64_t)(a0 + r) * lda + pr.a_off + k] : 0.f;
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    const bool inexact = __bfloat162float(b) != v;
+    bad |= inexact;
+    *reinterpret_cast<__nv_bfloat16*>(sA + core_off(r, k, KB)) = b;
+    if (split) {
+      const float r1 = __fsub_rn(v, __bfloat162float(b));
+      const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
+      const __nv_bfloat16 b3 = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(b2)));
+      *reinterpret_cast<__nv_bfloat16*>(sA2 + core_off(r, k, KB)) = b2;
+      *reinterpret_cast<__nv_bfloat16*>(sA3 + core_off(r, k, KB)) = b3;
     }
   }
-  {  // codewords: one 16-byte core row per step
+  const int bpl = (pr.b_planes == 2 && !bsplit) ? 0 : pr.b_planes;  // a second plane needs its smem
+  {  // codewords: one 16-byte core row per step (and the second plane)
     const int q8 = kpad >> 3;
     for (int e = tid; e < nt * q8; e += 128) {
       const int r = e / q8, k = (e - r * q8) << 3;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (n0 + r < pr.nb) v = *reinterpret_cast<const uint4*>(pr.Bb + (int64_t)(n0 + r) * kpad + k);
+      uint4 v = make_uint4(0u, 0u, 0u, 0u), v2 = make_uint4(0u, 0u, 0u, 0u);
+      if (n0 + r < pr.nb) {
+        v = *reinterpret_cast<const uint4*>(pr.Bb + (int64_t)(n0 + r) * kpad + k);
+        if (bpl == 2) v2 = *reinterpret_cast<const uint4*>(pr.Bb2 + (int64_t)(n0 + r) * kpad + k);
+      }
       *reinterpret_cast<uint4*>(sB + core_off(r, k, KB)) = v;
+      if (bpl == 2) *reinterpret_cast<uint4*>(sB2 + core_off(r, k, KB)) = v2;
     }
   }
   for (int c = tid; c < nt; c += 128) bn_s[c] = n0 + c < pr.nb ? pr.bn[n0 + c] : 0.f;
-  bad = __syncthreads_or(bad) || !pr.b_exact;
+  bad = __syncthreads_or(bad);
+  // A inexact (real-valued queries): three planes when the launch allows them; B in
+  // one or two exact planes; otherwise the CUDA cores
+  const bool use_split = bad && split && bpl > 0;
+  bad = (bad && !use_split) || bpl == 0;
+  const int planes = use_split ? 3 : 1;
   const int row = warp * 32 + lane, ga = a0 + row;
   bool done = false;
   if (!bad) {
@@ -124,11 +137,18 @@ __global__ void __launch_bounds__(128) tc_table_kernel(const float* __restrict__
     const uint32_t idesc =
         (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
     if (tid == 0) {
-      for (int kk = 0; kk < kpad / 16; ++kk) {
-        const uint64_t ad = smem_desc(smem_u32(sA) + kk * 256, 128, KB * 128);
-        const uint64_t bd = smem_desc(smem_u32(sB) + kk * 256, 128, KB * 128);
-        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                     ::"r"(tm), "l"(ad), "l"(bd), "r"(idesc), "r"(kk > 0 ? 1u : 0u));
+      for (int pl = 0; pl < planes; ++pl) {
+        const unsigned char* ap = pl == 0 ? sA : (pl == 1 ? sA2 : sA3);
+        for (int pb = 0; pb < bpl; ++pb) {
+          const unsigned char* bp = pb == 0 ? sB : sB2;
+          for (int kk = 0; kk < kpad / 16; ++kk) {
+            const uint64_t ad = smem_desc(smem_u32(ap) + kk * 256, 128, KB * 128);
+            const uint64_t bd = smem_desc(smem_u32(bp) + kk * 256, 128, KB * 128);
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                ::"r"(tm), "l"(ad), "l"(bd), "r"(idesc), "r"((pl > 0 || pb > 0 || kk > 0) ? 1u : 0u));
+          }
+        }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar)));
     }
@@ -145,9 +165,17 @@ __global__ void __launch_bounds__(128) tc_table_kernel(const float* __restrict__
       asm volatile("tcgen05.fence::after_thread_sync;");
       float an = 0.f;
       if (MODE == MODE_SQ) {
-        for (int k = 0; k < pr.dim; ++k) {
-          const float v = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(sA + core_off(row, k, KB)));
-          an = fmaf(v, v, an);
+        if (use_split) {  // ||a||^2 of the FP32 row
+          if (ga < na)
+            for (int k = 0; k < pr.dim; ++k) {
+              const float v = A[(int64_t)ga * lda + pr.a_off + k];
+              an = fmaf(v, v, an);
+            }
+        } else {
+          for (int k = 0; k < pr.dim; ++k) {
+            const float v = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(sA + core_off(row, k, KB)));
+            an = fmaf(v, v, an);
+          }
         }
       }
       const bool vec = ((pr.ldo | pr.o_off) & 3) == 0;
@@ -207,20 +235,26 @@ __global__ void __launch_bounds__(128) tc_table_kernel(const float* __restrict__
 // BF16 copy (K padded to kpad) and squared norms of n rows of dim floats; sets
 // *inexact if a value is not exactly representable in BF16.
 __global__ void bf16_rows_kernel(const float* __restrict__ X, int64_t n, int dim, int kpad,
-                                 __nv_bfloat16* __restrict__ Xb, float* __restrict__ norms, int* inexact) {
+                                 __nv_bfloat16* __restrict__ Xb, float* __restrict__ norms, int* inexact,
+                                 __nv_bfloat16* __restrict__ Xb2, int* inexact2) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   float s = 0.f;
-  int bad = 0;
+  int bad = 0, bad2 = 0;
   for (int k = 0; k < kpad; ++k) {
     const float v = k < dim ? X[r * dim + k] : 0.f;
     const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    const float rest = __fsub_rn(v, __bfloat162float(b));
+    const __nv_bfloat16 b2 = __float2bfloat16_rn(rest);
     bad |= __bfloat162float(b) != v;
+    bad2 |= __bfloat162float(b2) != rest;
     Xb[r * kpad + k] = b;
+    Xb2[r * kpad + k] = b2;
     s = fmaf(v, v, s);
   }
   norms[r] = s;
   if (bad) atomicExch(inexact, 1);
+  if (bad2) atomicExch(inexact2, 1);
 }
 
 // X[i][k][t] = 2 * sum_d C[i][k*s + d] * R[kbase + k][t][d]
@@ -317,30 +351,41 @@ void launch_query_tables(const bpq_index& ix, const float* q, int64_t nq, float*
   if (d1 || d2) {
     TcProblems pp{};
     int np = 0;
-    const int ex = ix.coarse_bf16_exact ? 1 : 0;
+    const int bp = ix.coarse_bf16_exact ? 1 : (ix.coarse_bf16x2_exact ? 2 : 0);
     if (d1)
       pp.p[np++] = TcProblem{ix.C1b.as<__nv_bfloat16>(), ix.C1.as<float>(), ix.n1.as<float>(), d1, 0, T, ix.h, ix.kh,
-                             T, 0, ex};
+                             T, 0, bp, ix.C1b2.as<__nv_bfloat16>()};
     if (d2)
       pp.p[np++] = TcProblem{ix.C2b.as<__nv_bfloat16>(), ix.C2.as<float>(), ix.n2.as<float>(), d2, ix.h, T, ix.h,
-                             ix.kh, T, 0, ex};
-    const size_t smem = (size_t)(TC_M + TC_N) * ix.kh * 2;
+                             ix.kh, T, 0, bp, ix.C2b2.as<__nv_bfloat16>()};
+    // the split planes of real-valued queries (OPQ) and the codewords' second plane,
+    // when they fit beside the operands
+    const size_t base = (size_t)(TC_M + TC_N) * ix.kh * 2, planes = (size_t)2 * TC_M * ix.kh * 2;
+    const size_t bplane = bp == 2 ? (size_t)TC_N * ix.kh * 2 : 0;
+    const int split = ix.opq && base + planes + bplane <= 220 * 1024;
+    const int bsplit = bp == 2 && base + (split ? planes : 0) + bplane <= 220 * 1024;
+    const size_t smem = base + (split ? planes : 0) + (bsplit ? bplane : 0);
     BPQ_CUDA(cudaFuncSetAttribute(tc_table_kernel<MODE_SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((T + TC_N - 1) / TC_N, ty, np);
-    tc_table_kernel<MODE_SQ><<<grid, 128, smem, st>>>(q, D, (int)nq, pp, status);
+    tc_table_kernel<MODE_SQ><<<grid, 128, smem, st>>>(q, D, (int)nq, pp, status, split, bsplit);
     check_launch("coarse table kernel");
   }
   if (lut) {
     BPQ_CHECK(M <= MAXP, BPQ_EINVAL, "M too large for the table kernel");
     TcProblems pp{};
-    const int ex = ix.R_bf16_exact ? 1 : 0;
+    const int bp = ix.R_bf16_exact ? 1 : (ix.R_bf16x2_exact ? 2 : 0);
     for (int k = 0; k < M; ++k)
       pp.p[k] = TcProblem{ix.Rb.as<__nv_bfloat16>() + (int64_t)k * KSUB * ix.ks, ix.R.as<float>() + (int64_t)k * KSUB * ix.s,
-                          ix.nR.as<float>() + (int64_t)k * KSUB, lut, k * ix.s, KSUB, ix.s, ix.ks, M * KSUB, k * KSUB, ex};
-    const size_t smem = (size_t)(TC_M + TC_N) * ix.ks * 2;
+                          ix.nR.as<float>() + (int64_t)k * KSUB, lut, k * ix.s, KSUB, ix.s, ix.ks, M * KSUB, k * KSUB,
+                          bp, ix.Rb2.as<__nv_bfloat16>() + (int64_t)k * KSUB * ix.ks};
+    const size_t base = (size_t)(TC_M + TC_N) * ix.ks * 2, planes = (size_t)2 * TC_M * ix.ks * 2;
+    const size_t bplane = bp == 2 ? (size_t)TC_N * ix.ks * 2 : 0;
+    const int split = ix.opq && base + planes + bplane <= 220 * 1024;
+    const int bsplit = bp == 2 && base + (split ? planes : 0) + bplane <= 220 * 1024;
+    const size_t smem = base + (split ? planes : 0) + (bsplit ? bplane : 0);
     BPQ_CUDA(cudaFuncSetAttribute(tc_table_kernel<MODE_LUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(1, ty, M);
-    tc_table_kernel<MODE_LUT><<<grid, 128, smem, st>>>(q_lut, D, (int)nq, pp, status);
+    tc_table_kernel<MODE_LUT><<<grid, 128, smem, st>>>(q_lut, D, (int)nq, pp, status, split, bsplit);
     check_launch("pq table kernel");
   }
 }
@@ -365,25 +410,31 @@ void build_fbpq_tables(bpq_index& ix, cudaStream_t st) {
   ix.C1b.alloc((size_t)T * ix.kh * 2);
   ix.C2b.alloc((size_t)T * ix.kh * 2);
   ix.Rb.alloc((size_t)nR * ix.ks * 2);
+  ix.C1b2.alloc((size_t)T * ix.kh * 2);
+  ix.C2b2.alloc((size_t)T * ix.kh * 2);
+  ix.Rb2.alloc((size_t)nR * ix.ks * 2);
   ix.n1.alloc((size_t)T * 4);
   ix.n2.alloc((size_t)T * 4);
   ix.nR.alloc((size_t)nR * 4);
   DevBuf flags;
-  flags.alloc(8);
-  BPQ_CUDA(cudaMemsetAsync(flags.p, 0, 8, st));
-  int* fl = flags.as<int>();
+  flags.alloc(16);
+  BPQ_CUDA(cudaMemsetAsync(flags.p, 0, 16, st));
+  int* fl = flags.as<int>();  // [coarse, R] one plane inexact, [coarse, R] two planes inexact
   bf16_rows_kernel<<<(T + 255) / 256, 256, 0, st>>>(ix.C1.as<float>(), T, ix.h, ix.kh, ix.C1b.as<__nv_bfloat16>(),
-                                                    ix.n1.as<float>(), fl);
+                                                    ix.n1.as<float>(), fl, ix.C1b2.as<__nv_bfloat16>(), fl + 2);
   bf16_rows_kernel<<<(T + 255) / 256, 256, 0, st>>>(ix.C2.as<float>(), T, ix.h, ix.kh, ix.C2b.as<__nv_bfloat16>(),
-                                                    ix.n2.as<float>(), fl);
+                                                    ix.n2.as<float>(), fl, ix.C2b2.as<__nv_bfloat16>(), fl + 2);
   bf16_rows_kernel<<<(int)((nR + 255) / 256), 256, 0, st>>>(ix.R.as<float>(), nR, ix.s, ix.ks,
-                                                            ix.Rb.as<__nv_bfloat16>(), ix.nR.as<float>(), fl + 1);
+                                                            ix.Rb.as<__nv_bfloat16>(), ix.nR.as<float>(), fl + 1,
+                                                            ix.Rb2.as<__nv_bfloat16>(), fl + 3);
   check_launch("table operand kernel");
-  int h_fl[2] = {1, 1};
-  BPQ_CUDA(cudaMemcpyAsync(h_fl, fl, 8, cudaMemcpyDeviceToHost, st));
+  int h_fl[4] = {1, 1, 1, 1};
+  BPQ_CUDA(cudaMemcpyAsync(h_fl, fl, 16, cudaMemcpyDeviceToHost, st));
   BPQ_CUDA(cudaStreamSynchronize(st));
   ix.coarse_bf16_exact = h_fl[0] == 0;
   ix.R_bf16_exact = h_fl[1] == 0;
+  ix.coarse_bf16x2_exact = h_fl[2] == 0;
+  ix.R_bf16x2_exact = h_fl[3] == 0;
 }
 
 }  // namespace bpq
