@@ -192,6 +192,24 @@ int bpq_add(bpq_index* idx, const float* x_dev, int64_t n, const int32_t* ids_de
 int bpq_finalize(bpq_index* idx, void* stream);
 
 /*
+ * bpq_set_global_counts — make this index a point shard of a larger index (the
+ * layout for an index that does not fit one GPU; queries are independent,
+ * §2.3.3, so the shards need no exchange but the final merge).  counts_host:
+ * T*T int64, the number of points of each cell (i*T + j) in the WHOLE index (the
+ * sum of every shard's counts).  From then on every search of this index
+ * traverses the cells with these counts -- the stopping rule "the visited cells
+ * hold at least L points" of §2.3.3 is the whole index's, so every shard visits
+ * the same cells and reports the same L' -- and scores only the points this
+ * shard holds; the k best of each shard, merged by (distance, id), are exactly
+ * the whole index's answer.  NULL clears the setting.  Call after bpq_finalize
+ * (which clears it, as the shard's lists change); not saved by bpq_save.
+ * Errors: BPQ_ESTATE before bpq_finalize; BPQ_EINVAL for a count outside
+ * [0, 2^32) or below this shard's count of the same cell.
+ * bpq_search_noalloc rejects a shard.
+ */
+int bpq_set_global_counts(bpq_index* idx, const int64_t* counts_host);
+
+/*
  * bpq_query_tables — per-query tables of §3.1 for nq queries (queries_dev:
  * nq x D float32): d1_dev, d2_dev: nq x T squared distances ||q^1 - c^1_i||^2,
  * ||q^2 - c^2_j||^2 (Eqs. 2-3); lut_dev (may be NULL): nq x M x 256 entries

@@ -67,6 +67,7 @@ _SIGS = {
     "bpq_add": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     "bpq_reconstruction_error": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P]),
     "bpq_finalize": (ctypes.c_int, [_P, _P]),
+    "bpq_set_global_counts": (ctypes.c_int, [_P, _P]),
     "bpq_query_tables": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P]),
     "bpq_search_workspace_size": (ctypes.c_size_t, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                                     ctypes.c_int32]),
@@ -257,6 +258,26 @@ class Index:
 
     def finalize(self, stream=None):
         _check(lib().bpq_finalize(self._h, _stream(stream)))
+
+    def cell_counts(self):
+        """Points per cell (i*T + j) of this index's lists: int64 numpy (T*T,)."""
+        import numpy as np
+        off = self.arrays()["offsets"].cpu().numpy().view(np.uint32).astype(np.int64)
+        return np.diff(off)
+
+    def set_global_counts(self, counts):
+        """Make this index a point shard: the whole index's per-cell counts (int64, T*T)
+        drive the traversal, the shard's own lists the scan (bpq_set_global_counts).
+        None clears it."""
+        import numpy as np
+        if counts is None:
+            _check(lib().bpq_set_global_counts(self._h, None))
+            return
+        c = np.ascontiguousarray(counts, dtype=np.int64)
+        p = self.params
+        if c.shape != (p.T * p.T,):
+            raise ValueError(f"counts must have shape ({p.T * p.T},)")
+        _check(lib().bpq_set_global_counts(self._h, c.ctypes.data))
 
     # -- introspection --------------------------------------------------------
     def info(self):

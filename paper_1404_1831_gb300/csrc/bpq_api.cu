@@ -4,10 +4,15 @@
 // enqueued on the caller's stream, chunk by chunk when the workspace is small.
 #include <algorithm>
 #include <cstddef>
+#include <cstdint>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "bpq_internal.cuh"
@@ -119,6 +124,8 @@ struct Layout {
   size_t hb_qbase, hb_qrows, hb_qbits, hb_hmap, hb_ctr, hb_fb, hb_tab;
   size_t wq_ctr, wq_items, wq_merges, wq_pids, wq_pdists;  // work-queue scan
   size_t rq_c, rq_r;  // OPQ: rot0 q and B rot0 q of the chunk's queries
+  size_t fb_list, fb_n, fb_handed;  // the traversal's handed-over queries (overlapped passes)
+  bool overlap;
   int64_t cap, hb_slots;
   bool wq;
 };
@@ -148,7 +155,10 @@ Layout layout(const bpq_index& ix, int64_t nq, int64_t L_max, int scorer, bool w
   o = align_up(o + (size_t)nq * ix.p.T * 4);
   l.lut = o;
   if (uses_lut(scorer) && with_cells) o = align_up(o + (size_t)nq * ix.p.M * KSUB * 4);
-  l.cap = std::max<int64_t>(1, std::min<int64_t>(L_max, std::max<int64_t>(ix.n_nonempty, 1)));
+  // visited cells per query: at most the non-empty cells the traversal sees (the
+  // whole index's for a point shard)
+  const int64_t nonempty = ix.goffsets.p ? ix.g_nonempty : ix.n_nonempty;
+  l.cap = std::max<int64_t>(1, std::min<int64_t>(L_max, std::max<int64_t>(nonempty, 1)));
   l.cells = o;
   if (with_cells) o = align_up(o + (size_t)nq * l.cap * sizeof(bpq_cell));
   l.ncells = o;
@@ -181,6 +191,17 @@ Layout layout(const bpq_index& ix, int64_t nq, int64_t L_max, int scorer, bool w
     o = align_up(o + (size_t)l.hb_slots * ix.m2 * KSUB * 4);
   }
   l.wq = with_cells && work_queue_used(work_W, scorer, k);
+  // FBPQ segment scan: the traversal's CTA pass and the scan of the queries it
+  // takes run beside the scan of the others
+  l.overlap = with_cells && scorer == BPQ_SCORER_FBPQ && k <= 128 && !l.wq && ix.p.T <= 1024 && !ix.goffsets.p;
+  if (l.overlap) {
+    l.fb_n = o;
+    o = align_up(o + 4);
+    l.fb_list = o;
+    o = align_up(o + (size_t)nq * 4);
+    l.fb_handed = o;
+    o = align_up(o + (size_t)nq);
+  }
   if (l.wq) {
     const size_t parts = (size_t)nq * SCAN_MAX_ITEMS;
     l.wq_ctr = o;
@@ -211,6 +232,16 @@ int64_t read_L(const int64_t* L_host, int64_t L_stride, int64_t nq, std::vector<
     if (per_query && L_stride) (*per_query)[i] = (int32_t)v;
   }
   return L_max;
+}
+
+// The traversal's cell counts and mean points per non-empty cell: the whole
+// index's for a point shard, else the index's own.
+const uint32_t* traversal_offsets(const bpq_index& ix) {
+  return ix.goffsets.p ? ix.goffsets.as<uint32_t>() : ix.offsets.as<uint32_t>();
+}
+float traversal_rho(const bpq_index& ix) {
+  if (ix.goffsets.p) return (float)((double)ix.g_points / (double)std::max<int64_t>(1, ix.g_nonempty));
+  return (float)((double)ix.n_points / (double)std::max<int64_t>(1, ix.n_nonempty));
 }
 
 void check_searchable(const bpq_index* ix) {
@@ -264,6 +295,38 @@ void check_scorer(const bpq_index& ix, int scorer) {
 // chunks that fit the workspace.  L32_pinned (optional, per-query budgets only):
 // the same budgets as int32 in page-locked host memory, copied from there so that
 // no pageable copy stalls the host on the stream.
+namespace {
+
+// A second stream per (device, caller stream) for the overlapped passes, with
+// the fork and join events; created on first use and kept for the process.
+struct AuxStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  std::mutex m;  // one caller at a time enqueues the fork ... join sequence
+};
+
+AuxStream* aux_stream(cudaStream_t st) {
+  static std::mutex pool_m;
+  static std::map<std::pair<int, cudaStream_t>, std::unique_ptr<AuxStream>> pool;
+  int dev = 0;
+  BPQ_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> g(pool_m);
+  auto it = pool.find({dev, st});
+  if (it != pool.end()) return it->second.get();
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  BPQ_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone || pool.size() >= 256) return nullptr;  // no new stream: one pass after the other
+  auto a = std::make_unique<AuxStream>();
+  BPQ_CUDA(cudaStreamCreateWithFlags(&a->s, cudaStreamNonBlocking));
+  BPQ_CUDA(cudaEventCreateWithFlags(&a->fork, cudaEventDisableTiming));
+  BPQ_CUDA(cudaEventCreateWithFlags(&a->join, cudaEventDisableTiming));
+  AuxStream* r = a.get();
+  pool.emplace(std::make_pair(dev, st), std::move(a));
+  return r;
+}
+
+}  // namespace
+
 void bpq::run_queries(const bpq_index& ix, const float* q, int64_t nq, const int64_t* L_host, int64_t L_stride,
                       int k, int scorer, int32_t* out_ids, float* out_dists, bpq_cell* user_cells, int32_t user_cap,
                       int32_t* user_ncells, int64_t* user_npoints, void* ws, size_t ws_bytes, cudaStream_t st,
@@ -325,7 +388,7 @@ void bpq::run_queries(const bpq_index& ix, const float* q, int64_t nq, const int
   const Layout l = lay(chunk);
   char* w = static_cast<char*>(ws);
   BPQ_CUDA(cudaMemsetAsync(w + l.status, 0, 4, st));
-  const float rho = (float)((double)ix.n_points / (double)std::max<int64_t>(1, ix.n_nonempty));
+  const float rho = traversal_rho(ix);
   for (int64_t c0 = 0; c0 < nq; c0 += chunk) {
     const int64_t nc = std::min(chunk, nq - c0);
     const float* qc = q + c0 * ix.p.D;
@@ -347,7 +410,7 @@ void bpq::run_queries(const bpq_index& ix, const float* q, int64_t nq, const int
     TraverseArgs ta{};
     ta.d1 = d1;
     ta.d2 = d2;
-    ta.offsets = ix.offsets.as<uint32_t>();
+    ta.offsets = traversal_offsets(ix);
     if (L_stride) {
       BPQ_CUDA(cudaMemcpyAsync(w + l.L, (L32_pinned ? L32_pinned : Lq.data()) + c0, nc * 4, cudaMemcpyHostToDevice, st));
       ta.L = reinterpret_cast<const int32_t*>(w + l.L);
@@ -371,10 +434,37 @@ void bpq::run_queries(const bpq_index& ix, const float* q, int64_t nq, const int
       ta.ncells = user_ncells + c0;
       ta.npoints = user_npoints + c0;
     }
-    launch_traverse(ta, st);
-    if (!scan) continue;
     ScanArgs sa = scan_args(ix, qres, nc, lut, ta.cells, ta.ncells, ta.cap, k, out_ids + c0 * k,
                             out_dists + c0 * k, reinterpret_cast<int32_t*>(w + l.qcounter));
+    AuxStream* aux = (scan && l.overlap) ? aux_stream(st) : nullptr;
+    if (aux) {
+      // the warp pass lists the queries it hands over; the CTA pass for them, then
+      // their scan, run on the second stream beside the scan of the other queries
+      ta.fb_n = reinterpret_cast<int32_t*>(w + l.fb_n);
+      ta.fb_list = reinterpret_cast<int32_t*>(w + l.fb_list);
+      ta.handed = reinterpret_cast<uint8_t*>(w + l.fb_handed);
+      BPQ_CUDA(cudaMemsetAsync(ta.fb_n, 0, 4, st));
+      if (launch_traverse_warp(ta, st)) {
+        std::lock_guard<std::mutex> g(aux->m);
+        BPQ_CUDA(cudaEventRecord(aux->fork, st));
+        BPQ_CUDA(cudaStreamWaitEvent(aux->s, aux->fork, 0));
+        launch_traverse_marked(ta, aux->s);
+        ScanArgs sb = sa;
+        sb.sel = ta.fb_list;
+        sb.sel_n = ta.fb_n;
+        launch_scan(sb, scorer, aux->s);
+        sa.skip = ta.handed;
+        launch_scan(sa, scorer, st);
+        BPQ_CUDA(cudaEventRecord(aux->join, aux->s));
+        BPQ_CUDA(cudaStreamWaitEvent(st, aux->join, 0));
+      } else {
+        launch_scan(sa, scorer, st);  // the CTA pass took every query
+      }
+      continue;
+    }
+    launch_traverse(ta, st);
+    if (ix.goffsets.p) launch_localize_cells(ta, ix.offsets.as<uint32_t>(), st);
+    if (!scan) continue;
     if (hb) {
       // per-(query, visited half-cell) tables on the tensor cores, then the M-lookup scan
       HbpqArgs h{};
@@ -472,7 +562,7 @@ void run_shortlist(const bpq_index& ix, const float* q, int64_t nq, const int64_
   const ShortlistLayout l = shortlist_layout(ix, chunk, L_max, S);
   char* w = static_cast<char*>(ws);
   BPQ_CUDA(cudaMemsetAsync(w + l.base.status, 0, 4, st));
-  const float rho = (float)((double)ix.n_points / (double)std::max<int64_t>(1, ix.n_nonempty));
+  const float rho = traversal_rho(ix);
   for (int64_t c0 = 0; c0 < nq; c0 += chunk) {
     const int64_t nc = std::min(chunk, nq - c0);
     const float* qc = q + c0 * ix.p.D;
@@ -496,7 +586,7 @@ void run_shortlist(const bpq_index& ix, const float* q, int64_t nq, const int64_
     TraverseArgs ta{};
     ta.d1 = d1;
     ta.d2 = d2;
-    ta.offsets = ix.offsets.as<uint32_t>();
+    ta.offsets = traversal_offsets(ix);
     if (L_stride) {
       BPQ_CUDA(cudaMemcpyAsync(w + l.base.L, Lq.data() + c0, nc * 4, cudaMemcpyHostToDevice, st));
       ta.L = reinterpret_cast<const int32_t*>(w + l.base.L);
@@ -514,12 +604,14 @@ void run_shortlist(const bpq_index& ix, const float* q, int64_t nq, const int64_
     ta.ncells = reinterpret_cast<int32_t*>(w + l.base.ncells);
     ta.npoints = reinterpret_cast<int64_t*>(w + l.base.npoints);
     launch_traverse(ta, st);
+    if (ix.goffsets.p) launch_localize_cells(ta, ix.offsets.as<uint32_t>(), st);
     ScanArgs sa = scan_args(ix, qc, nc, lut, ta.cells, ta.ncells, ta.cap, S, nullptr, nullptr,
                             reinterpret_cast<int32_t*>(w + l.base.qcounter));
     sa.lut8 = static_cast<const uint8_t*>(lutr);
     sa.lut16 = static_cast<const uint16_t*>(lutr);
     sa.lut_scale = scale;
     sa.sl_out = sl;
+    sa.status = ta.status;
     launch_scan_reduced(sa, f16, st);
     RescoreArgs r{};
     r.sl = sl;
@@ -816,6 +908,46 @@ int bpq_finalize(bpq_index* ix, void* stream) {
     BPQ_CHECK(ix, BPQ_EINVAL, "index is NULL");
     DeviceGuard dg(ix->device);
     finalize_lists(*ix, static_cast<cudaStream_t>(stream));
+    ix->goffsets.release();  // the shard's lists changed: its whole-index counts must be set again
+    ix->g_points = ix->g_nonempty = 0;
+  });
+}
+
+int bpq_set_global_counts(bpq_index* ix, const int64_t* counts_host) {
+  return guard([&] {
+    check_searchable(ix);
+    DeviceGuard dg(ix->device);
+    if (!counts_host) {
+      ix->goffsets.release();
+      ix->g_points = ix->g_nonempty = 0;
+      return;
+    }
+    const int64_t nc = (int64_t)ix->p.T * ix->p.T;
+    BPQ_CHECK(ix->offsets.p, BPQ_ESTATE, "the index has no lists: call bpq_finalize first");
+    std::vector<uint32_t> loff((size_t)nc + 1);
+    BPQ_CUDA(cudaMemcpy(loff.data(), ix->offsets.p, loff.size() * 4, cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> g((size_t)nc + 1);
+    int64_t total = 0, nonempty = 0;
+    uint32_t run = 0;
+    for (int64_t c = 0; c < nc; ++c) {
+      const int64_t v = counts_host[c];
+      BPQ_CHECK(v >= 0 && v < ((int64_t)1 << 32), BPQ_EINVAL, "every count must be in [0, 2^32)");
+      BPQ_CHECK(v >= (int64_t)(loff[c + 1] - loff[c]), BPQ_EINVAL,
+                "a cell holds more points in this shard than in the whole index");
+      BPQ_CHECK(total <= INT64_MAX - v, BPQ_EINVAL, "the counts overflow");
+      g[c] = run;
+      run += (uint32_t)v;  // modulo 2^32: differences of neighbours are the counts
+      total += v;
+      nonempty += v > 0;
+    }
+    g[nc] = run;
+    DevBuf d;
+    d.alloc(g.size() * 4);
+    BPQ_CUDA(cudaMemcpy(d.p, g.data(), g.size() * 4, cudaMemcpyHostToDevice));
+    std::swap(ix->goffsets.p, d.p);
+    std::swap(ix->goffsets.bytes, d.bytes);
+    ix->g_points = total;
+    ix->g_nonempty = nonempty;
   });
 }
 

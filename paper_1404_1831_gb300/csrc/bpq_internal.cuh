@@ -235,6 +235,11 @@ struct bpq_index {
   // log2 mean L); a class found here overrides scan_work_W
   std::map<uint64_t, int32_t> tuned_W;
   int64_t n_points = 0, n_nonempty = 0, max_cell = 0;
+  // point shard (bpq_set_global_counts): the whole index's per-cell counts as a
+  // prefix modulo 2^32 (differences give the counts), its points and non-empty
+  // cells; the traversal runs on these, the scan on the shard's own lists
+  bpq::DevBuf goffsets;
+  int64_t g_points = 0, g_nonempty = 0;
   // workspace owned by bpq_search_host
   bpq::DevBuf host_ws, host_q, host_ids, host_dists;
 };
@@ -300,8 +305,23 @@ struct TraverseArgs {
   int64_t* npoints;
   int32_t* status;   // single word, set to 1 on overflow
   int64_t nq;
+  // optional (T <= the warp path's limit): the warp kernel lists the queries it
+  // hands over in fb_list[0 .. *fb_n) (*fb_n zeroed by the caller) and writes
+  // handed[q] = 1 for them, 0 for the others; the CTA pass then takes the list
+  int32_t* fb_list;
+  int32_t* fb_n;
+  uint8_t* handed;
 };
 void launch_traverse(const TraverseArgs& a, cudaStream_t st);
+// The two passes of launch_traverse, for callers that overlap the second with
+// other work: the warp pass returns false when the CTA pass already ran for
+// every query (T above the warp path's limit) and there is no second pass.
+bool launch_traverse_warp(const TraverseArgs& a, cudaStream_t st);
+void launch_traverse_marked(const TraverseArgs& a, cudaStream_t st);
+// Point shard: after a traversal on the whole index's counts, each visited cell
+// gets the shard's list range (loff) and the cells the shard holds no point of
+// are dropped, in order.
+void launch_localize_cells(const TraverseArgs& a, const uint32_t* loff, cudaStream_t st);
 int traverse_band_capacity();
 
 // Scans (bpq_scan.cu).
@@ -333,7 +353,8 @@ struct ScanArgs {
   const uint8_t* lut8;     // nq x M x 256 (int8 form)
   const uint16_t* lut16;   // nq x M x 256 (fp16 form)
   const float* lut_scale;  // nq
-  uint64_t* sl_out;        // nq x k
+  uint64_t* sl_out;        // nq x k (any order; EMPTY padded)
+  int32_t* status;         // workspace status word (a bounded wait that gave up sets STATUS_TIMEOUT)
   // HBPQ table form: per-query slots and bitmaps (HbpqArgs) and the tables
   const int32_t* hb_qbase;
   const int32_t* hb_qrows;
@@ -342,6 +363,12 @@ struct ScanArgs {
   // reconstruction scans: when set, only the queries qlist[0 .. *qlist_n) are scored
   const int32_t* qlist;
   const int32_t* qlist_n;
+  // FBPQ segment scan (not the work-queue form): when sel is set, only the queries
+  // sel[0 .. *sel_n) are scored; when skip is set, the queries with skip[q] != 0
+  // are left alone (another launch scores them)
+  const int32_t* sel;
+  const int32_t* sel_n;
+  const uint8_t* skip;
   // persistent work-queue scan (work_W > 0, segment scans only): items (q, first
   // cell, end cell, partial slot or -1), counters (zeroed by the launcher), merge
   // records (q, first slot, items) and the partial lists

@@ -90,6 +90,7 @@ extern "C" int bpq_search_noalloc(const bpq_index* ix, const float* queries_dev,
   if ((scorer == BPQ_SCORER_HBPQ) != (ix->p.variant == BPQ_VARIANT_LOCAL))
     return fail(BPQ_EINVAL, "scorer does not match the codebook variant");
   if (ix->opq) return fail(BPQ_EINVAL, "OPQ indexes need rotated query buffers: use bpq_search");
+  if (ix->goffsets.p) return fail(BPQ_EINVAL, "point shards (whole-index counts set) are searched by bpq_search");
   if (!L_host || (L_stride != 0 && L_stride != 1)) return fail(BPQ_EINVAL, "L must be given with stride 0 or 1");
   int64_t L_max = 0;
   for (int64_t i = 0; i < (L_stride ? nq : 1); ++i) {

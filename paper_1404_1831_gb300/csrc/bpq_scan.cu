@@ -264,18 +264,6 @@ __device__ void block_topk_prune(BlockTopK<NT, CAP>& tk, int k) {
   __syncthreads();
 }
 
-// Final, raw: the first k composites of the exact order (EMPTY padded).
-template <int NT, int CAP>
-__device__ void block_topk_finish_raw(BlockTopK<NT, CAP>& tk, int k, uint64_t* out) {
-  block_topk_prune<NT, CAP>(tk, k);
-  const int n = *tk.nbuf;
-  int n2 = 1;
-  while (n2 < n) n2 <<= 1;
-  for (int e = n + threadIdx.x; e < n2; e += NT) tk.buf[e] = EMPTY;
-  block_bitonic_sort(tk.buf, n2);
-  for (int r = threadIdx.x; r < k; r += NT) out[r] = r < n ? tk.buf[r] : EMPTY;
-}
-
 // Final: exact (distance, id) order of the buffer, first k written out.
 template <int NT, int CAP>
 __device__ void block_topk_finish(BlockTopK<NT, CAP>& tk, int k, int32_t* out_ids, float* out_dists) {
@@ -293,13 +281,15 @@ __device__ void block_topk_finish(BlockTopK<NT, CAP>& tk, int k, int32_t* out_id
 }
 
 // ---------------------------------------------------------------------------
-// FBPQ scan: one CTA per query.
+// FBPQ scan variants:
 //  FB_POINT : per-point cross term (one coalesced float per candidate)
 //  FB_TABLES: cross terms gathered from the X1 / X2 tables (2M lookups)
 //  FB_F16   : FP16 table (bpq_search_shortlist): score (key + cross) + s * the FP32
 //             sum, in sub-quantizer order, of M FP16 entries; ranked as FB_Q8
 //  FB_Q8    : int8 table (bpq_search_shortlist): score (key + cross) + s * sum of
 //             M int8 entries, ranked by (score, list position); no id is read
+// The round-based kernel below (one CTA per query) takes FB_TABLES and k > 128;
+// the warp-segment kernel further down FB_POINT with k <= 128 and the shortlists.
 // ---------------------------------------------------------------------------
 enum { FB_POINT = 0, FB_TABLES = 1, FB_Q8 = 2, FB_F16 = 3 };
 
@@ -329,7 +319,8 @@ using CodeVec = typename std::conditional<M == 16, uint4, uint2>::type;
 //  load in flight.
 template <int M, int VAR, int ILP, int CAP, int SUB>
 __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
-  constexpr bool POINT = VAR != FB_TABLES, Q8 = VAR == FB_Q8, F16 = VAR == FB_F16, RED = Q8 || F16;
+  static_assert(VAR == FB_POINT || VAR == FB_TABLES, "the shortlists run on the warp-segment scan");
+  constexpr bool POINT = VAR != FB_TABLES;
   constexpr int NT = 256, NW = NT / 32, CH = NT, M2 = M / 2;
   constexpr int PER = SUB / NT;      // candidates per thread in the cell map of a slice
   using TK = BlockTopK<NT, CAP>;
@@ -352,20 +343,9 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
   const int lane = threadIdx.x & 31;
   const int k = a.k;
 
-  const uint8_t* lut8 = reinterpret_cast<const uint8_t*>(lut);
-  const __half* lut16 = reinterpret_cast<const __half*>(lut);
   for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
     __syncthreads();
-    float scale = 0.f;
-    if (Q8) {
-      const uint4* src = reinterpret_cast<const uint4*>(a.lut8 + q * M * KSUB);
-      for (int t = threadIdx.x; t < M * KSUB / 16; t += NT) reinterpret_cast<uint4*>(lut)[t] = src[t];
-      scale = a.lut_scale[q];
-    } else if (F16) {
-      const uint4* src = reinterpret_cast<const uint4*>(a.lut16 + q * M * KSUB);
-      for (int t = threadIdx.x; t < M * KSUB / 8; t += NT) reinterpret_cast<uint4*>(lut)[t] = src[t];
-      scale = a.lut_scale[q];
-    } else {
+    {
       const float4* src = reinterpret_cast<const float4*>(a.lut + q * M * KSUB);
       for (int t = threadIdx.x; t < M * KSUB / 4; t += NT) reinterpret_cast<float4*>(lut)[t] = src[t];
     }
@@ -473,17 +453,7 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
             if (cidx[u] >= 0) {
               const int c = cidx[u];
               float part;
-              if (Q8) {
-                int isum = 0;
-#pragma unroll
-                for (int kk = 0; kk < M; ++kk) isum += lut8[kk * KSUB + code[u].byte(kk)];
-                part = __fmul_rn(scale, (float)isum);
-              } else if (F16) {
-                float hs = 0.f;  // FP32 additions in sub-quantizer order
-#pragma unroll
-                for (int kk = 0; kk < M; ++kk) hs = __fadd_rn(hs, __half2float(lut16[kk * KSUB + code[u].byte(kk)]));
-                part = __fmul_rn(scale, hs);
-              } else if (POINT) {
+              if (POINT) {
                 part = pc[u];
 #pragma unroll
                 for (int kk = 0; kk < M; ++kk) part += lut[kk * KSUB + code[u].byte(kk)];
@@ -498,10 +468,10 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
                   part += lut[kk * KSUB + b] + xv;
                 }
               }
-              const float dist = RED ? __fadd_rn(__fadd_rn(c_key[c], pc[u]), part) : c_key[c] + part;
+              const float dist = c_key[c] + part;
               const uint32_t o = f2ord(dist);
               if (o <= th_hi) {
-                comp = ((uint64_t)o << 32) | (RED ? pos[u] : (uint32_t)__ldg(a.ids + pos[u]));
+                comp = ((uint64_t)o << 32) | (uint32_t)__ldg(a.ids + pos[u]);
                 acc = comp <= th;
               }
             }
@@ -519,10 +489,7 @@ __global__ void __launch_bounds__(256) fbpq_scan_kernel(ScanArgs a) {
         __syncthreads();
       }
     }
-    if (RED)
-      block_topk_finish_raw<NT, CAP>(tk, k, a.sl_out + q * k);
-    else
-      block_topk_finish<NT, CAP>(tk, k, a.out_ids + q * k, a.out_dists + q * k);
+    block_topk_finish<NT, CAP>(tk, k, a.out_ids + q * k, a.out_dists + q * k);
   }
 }
 
@@ -721,16 +688,148 @@ __device__ uint32_t block_cut(const uint64_t* a, int n, int k, int* red) {
   return (uint32_t)hi;
 }
 
+// Shortlists (bpq_search_shortlist): the S best (score, list position) composites
+// of a query.  S is up to 1024, more than a warp buffer holds, so the warps move
+// their buffered entries into one block buffer of BBC entries, one warp at a
+// time (a lock in shared memory); when it nears its capacity that warp cuts it
+// to the entries at or below a value v with at least S entries <= v (a count
+// bisection on the score bits over the buffer, stopped once S .. S + 32 remain)
+// and lowers the block threshold to (v, any position).  If a tie group at v
+// still fills the buffer, the cut is exact on the whole composite.
+
+// Entries of bb[0 .. n) with bits <= v kept in place (v on the whole composite
+// when `whole`, else on the score bits).  Warp-wide; returns the new count.
+__device__ int sl_compact(uint64_t* bb, int n, uint64_t v, bool whole) {
+  const int lane = threadIdx.x & 31;
+  int kept = 0;
+  for (int e0 = 0; e0 < n; e0 += 32) {
+    const int e = e0 + lane;
+    uint64_t x = 0;
+    bool keep = false;
+    if (e < n) {
+      x = bb[e];
+      keep = whole ? x <= v : (x >> 32) <= v;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    __syncwarp();  // this step's entries are read before any is overwritten
+    if (keep) bb[kept + __popc(m & lanemask_lt())] = x;
+    kept += __popc(m);
+  }
+  __syncwarp();
+  return kept;
+}
+
+// Number of entries of bb[0 .. n) with score bits <= hi (hi_eq: == hi) and
+// position bits <= lo_max.  Warp-wide.
+__device__ int sl_count(const uint64_t* bb, int n, uint32_t hi, bool hi_eq, long long lo_max) {
+  const int lane = threadIdx.x & 31;
+  int c = 0;
+  for (int e = lane; e < n; e += 32) {
+    const uint64_t x = bb[e];
+    const uint32_t h = (uint32_t)(x >> 32);
+    c += ((hi_eq ? h == hi : h <= hi) && (long long)(uint32_t)x <= lo_max) ? 1 : 0;
+  }
+  return warp_sum(c);
+}
+
+template <int KW, int BBC>
+__device__ void sl_flush(const uint64_t* wb, int wn, int S, uint64_t* bb, int* bb_n, int* lock,
+                         unsigned long long* thr, int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  int ok = 1;
+  if (lane == 0) {
+    long long spins = 0;
+    while (atomicCAS(lock, 0, 1) != 0) {
+      if (++spins > (1ll << 24)) {  // never expected: the holder is a warp of this CTA doing bounded work
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) {
+    if (lane == 0 && status) atomicOr(status, STATUS_TIMEOUT);
+    __syncwarp();
+    return;
+  }
+  __threadfence_block();
+  const unsigned long long th = *(volatile unsigned long long*)thr;
+  int n = *(volatile int*)bb_n;
+  for (int e0 = 0; e0 < wn; e0 += 32) {
+    const int e = e0 + lane;
+    const uint64_t x = e < wn ? wb[e] : EMPTY;
+    const bool keep = e < wn && x <= th;
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) bb[n + __popc(m & lanemask_lt())] = x;
+    n += __popc(m);
+  }
+  __syncwarp();
+  if (n > BBC - KW) {
+    uint32_t mn = 0xffffffffu, mx = 0u;
+    for (int e = lane; e < n; e += 32) {
+      const uint32_t h = (uint32_t)(bb[e] >> 32);
+      mn = min(mn, h);
+      mx = max(mx, h);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    long long lo = (long long)mn - 1, hi = mx;  // count(<= hi) >= S > count(<= lo)
+    while (hi - lo > 1) {
+      const uint32_t mid = (uint32_t)(lo + ((hi - lo) >> 1));
+      const int c = sl_count(bb, n, mid, false, 0xffffffffll);
+      if (c >= S) {
+        hi = mid;
+        if (c <= S + 32) break;
+      } else {
+        lo = mid;
+      }
+    }
+    const uint32_t v = (uint32_t)hi;
+    unsigned long long nt = ((unsigned long long)v << 32) | 0xffffffffull;
+    if (sl_count(bb, n, v, false, 0xffffffffll) > BBC - KW) {
+      // a tie group at v: the exact S-th composite, bisecting the positions at v
+      const int need = S - (v > 0 ? sl_count(bb, n, v - 1, false, 0xffffffffll) : 0);
+      long long plo = -1, phi = 0xffffffffll;  // count(pos <= phi) >= need > count(pos <= plo)
+      while (phi - plo > 1) {
+        const long long mid = plo + ((phi - plo) >> 1);
+        if (sl_count(bb, n, v, true, mid) >= need) phi = mid; else plo = mid;
+      }
+      nt = ((unsigned long long)v << 32) | (uint32_t)phi;
+      n = sl_compact(bb, n, nt, true);
+    } else {
+      n = sl_compact(bb, n, v, false);
+    }
+    if (lane == 0 && nt < *(volatile unsigned long long*)thr) *(volatile unsigned long long*)thr = nt;
+  }
+  if (lane == 0) *(volatile int*)bb_n = n;
+  __threadfence_block();
+  __syncwarp();
+  if (lane == 0) atomicExch(lock, 0);
+}
+
 // HB = true: the same scan for HBPQ's table form (§3.2): a candidate of cell (i, j)
 // costs the M lookups key(i, j) + sum_k A_i[k][c_k] + sum_k B_j[k][c_{M/2+k}] into
 // the per-(query, half-cell) tables built by the HBPQ table kernel (read through
 // the cache from global memory; the table slots of the query come from its row
 // and column bitmaps), and no cross term is read.
-template <int M, int NT, int D, int U, int KW, int CH, bool HB, bool WQ>
-__global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs a) {
+//
+// RV = FB_Q8 / FB_F16: the shortlist scan (the reduced-precision table and score
+// described with the variants above), with a block buffer of BBC entries (BBC - KW
+// >= S + 32; a small one for short shortlists keeps eight CTAs per SM); the S best
+// composites go to a.sl_out in any order.
+template <int M, int NT, int D, int U, int KW, int CH, bool HB, bool WQ, int RV, int BBC>
+__global__ void __launch_bounds__(NT, (HB || BBC > 1024) ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs a) {
   constexpr int NW = NT / 32, R = CH / NT, M2 = M / 2;
+  constexpr bool RED = RV == FB_Q8 || RV == FB_F16;
   static_assert(CH % NT == 0 && KW == 256, "shape (the exact prune keeps its payloads in the warp's 256 counters)");
-  constexpr int AREA0 = HB ? 0 : M * KSUB * 4;  // the query's table (FBPQ)
+  static_assert(RV == FB_POINT || (RED && !HB && !WQ && BBC > KW), "variant");
+  static_assert(RED || BBC == 0, "the block buffer is the shortlists'");
+  // the query's table: FP32 (FBPQ), int8 or FP16 (shortlists); none (HB)
+  constexpr int AREA0 = HB ? 0 : M * KSUB * (RV == FB_Q8 ? 1 : (RV == FB_F16 ? 2 : 4));
   constexpr int TWMAX = MAX_T / 32;
   using CV = CodeVec<M>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -738,10 +837,12 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
   uint32_t* hbits = reinterpret_cast<uint32_t*>(smem + AREA0);    // HB: 2 x TWMAX row / column bitmap words
   int* hpre = reinterpret_cast<int*>(hbits + (HB ? 2 * TWMAX : 0));  // HB: 2 x TWMAX bits below each word
   uint64_t* wbuf = reinterpret_cast<uint64_t*>(hpre + (HB ? 2 * TWMAX : 0));  // NW x KW
-  uint32_t* whist = reinterpret_cast<uint32_t*>(wbuf + NW * KW);  // NW x 256
-  int2* c_info = reinterpret_cast<int2*>(whist + NW * 256);       // CH: (begin - first candidate, key bits)
+  uint32_t* whist = reinterpret_cast<uint32_t*>(wbuf + NW * KW);  // NW x 256 (not the shortlists')
+  int2* c_info = reinterpret_cast<int2*>(whist + (RED ? 0 : NW * 256));  // CH: (begin - first candidate, key bits)
   int* c_pref = reinterpret_cast<int*>(c_info + CH);              // CH + 1: first candidate of each cell
   uint2* c_tab = reinterpret_cast<uint2*>(c_pref + CH + 2);       // HB, CH: table offsets (A_i, B_j) in floats
+  uint64_t* bb = reinterpret_cast<uint64_t*>(c_pref + CH + 2);    // RED, BBC: shortlist block buffer
+  __shared__ int bb_n, bb_lock;
   __shared__ int scan_tmp[NW + 1];
   __shared__ int cut_red[2 * NW];
   __shared__ int fcount;
@@ -774,8 +875,14 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
       part = itm.w >= 0;
       out_row = part ? itm.w : q;
     } else {
-      if (iter >= a.nq) break;
-      q = iter;
+      if (a.sel) {
+        if (iter >= *a.sel_n) break;
+        q = a.sel[iter];
+      } else {
+        if (iter >= a.nq) break;
+        q = iter;
+        if (a.skip && a.skip[q]) continue;  // uniform across the CTA
+      }
       c_hi = max(0, a.ncells[q]);
       out_row = q;
     }
@@ -797,10 +904,17 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
         hpre[x] = p;
       }
     } else {
-      const float4* src = reinterpret_cast<const float4*>(a.lut + q * M * KSUB);
-      for (int t = threadIdx.x; t < M * KSUB / 4; t += NT) reinterpret_cast<float4*>(lut)[t] = src[t];
+      const uint4* src = RV == FB_Q8    ? reinterpret_cast<const uint4*>(a.lut8 + q * M * KSUB)
+                         : RV == FB_F16 ? reinterpret_cast<const uint4*>(a.lut16 + q * M * KSUB)
+                                        : reinterpret_cast<const uint4*>(a.lut + q * M * KSUB);
+      for (int t = threadIdx.x; t < AREA0 / 16; t += NT) reinterpret_cast<uint4*>(lut)[t] = src[t];
     }
-    if (threadIdx.x == 0) thr = EMPTY;
+    const float scale = RED ? a.lut_scale[q] : 0.f;
+    if (threadIdx.x == 0) {
+      thr = EMPTY;
+      bb_n = 0;
+      bb_lock = 0;
+    }
     int wn = 0;  // entries in this warp's buffer (uniform across the warp)
     const bpq_cell* cl = a.cells + q * (int64_t)a.cap;
     for (int cs = c_lo; cs < c_hi; cs += CH) {
@@ -895,7 +1009,8 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
 #pragma unroll
         for (int d = 0; d < D; ++d) issue(d);
         for (int left = (e - s + 32 * U * WSTEP - 1) / (32 * U * WSTEP); left > 0; left -= D) {
-          const uint32_t th_hi = (uint32_t)(*(volatile unsigned long long*)&thr >> 32);
+          const unsigned long long th = *(volatile unsigned long long*)&thr;
+          const uint32_t th_hi = (uint32_t)(th >> 32);
 #pragma unroll
           for (int d = 0; d < D; ++d) {
             uint32_t o[U];
@@ -905,7 +1020,7 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
               acc[u] = false;
               o[u] = 0;
               if (spos[d][u] != NO_POS) {
-                float part = HB ? 0.f : sx[d][u];
+                float part = (HB || RED) ? 0.f : sx[d][u];
                 uint32_t wd[M / 4];
                 if constexpr (M == 16) {
                   wd[0] = scode[d][u].x;
@@ -923,6 +1038,20 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
                     const uint32_t c = (wd[kk >> 2] >> (8 * (kk & 3))) & 0xffu;
                     part += __ldg(a.hb_tables + (kk < M2 ? tb.x : tb.y) + (kk % M2) * KSUB + c);
                   }
+                } else if constexpr (RV == FB_Q8) {
+                  int isum = 0;  // exact integer sum of the int8 entries
+#pragma unroll
+                  for (int kk = 0; kk < M; ++kk)
+                    isum += (int)*reinterpret_cast<const uint8_t*>(lutb + kk * KSUB + ((wd[kk >> 2] >> (8 * (kk & 3))) & 0xffu));
+                  part = __fmul_rn(scale, (float)isum);
+                } else if constexpr (RV == FB_F16) {
+                  float hs = 0.f;  // FP32 additions in sub-quantizer order
+#pragma unroll
+                  for (int kk = 0; kk < M; ++kk) {
+                    const uint32_t off = ((wd[kk >> 2] >> (8 * (kk & 3))) & 0xffu) << 1;
+                    hs = __fadd_rn(hs, __half2float(*reinterpret_cast<const __half*>(lutb + kk * (KSUB * 2) + off)));
+                  }
+                  part = __fmul_rn(scale, hs);
                 } else {
 #pragma unroll
                   for (int kk = 0; kk < M; ++kk) {
@@ -930,8 +1059,13 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
                     part += *reinterpret_cast<const float*>(lutb + kk * (KSUB * 4) + off);
                   }
                 }
-                o[u] = f2ord(skey[d][u] + part);
-                acc[u] = o[u] <= th_hi;
+                if constexpr (RED) {  // (key + cross) + s * part, that order, no fused multiply-add
+                  o[u] = f2ord(__fadd_rn(__fadd_rn(skey[d][u], sx[d][u]), part));
+                  acc[u] = (((uint64_t)o[u] << 32) | spos[d][u]) <= th;
+                } else {
+                  o[u] = f2ord(skey[d][u] + part);
+                  acc[u] = o[u] <= th_hi;
+                }
               }
             }
 #pragma unroll
@@ -942,7 +1076,12 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
                 wn += __popc(m);
                 if (wn > KW - 32) {
                   __syncwarp();
-                  wn = warp_prune<KW>(wb, wn, k, hist, &thr, a.ids);
+                  if constexpr (RED) {
+                    sl_flush<KW, BBC>(wb, wn, k, bb, &bb_n, &bb_lock, &thr, a.status);
+                    wn = 0;
+                  } else {
+                    wn = warp_prune<KW>(wb, wn, k, hist, &thr, a.ids);
+                  }
                 }
               }
             }
@@ -951,6 +1090,23 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
         }
       }
     }
+    if constexpr (RED) {
+      // final (shortlist): the last entries of every warp into the block buffer
+      // (it then holds at most BBC - KW), sorted when more than S: the S smallest
+      // composites are the shortlist
+      if (wn > 0) sl_flush<KW, BBC>(wb, wn, k, bb, &bb_n, &bb_lock, &thr, a.status);
+      __syncthreads();
+      const int n = bb_n;
+      uint64_t* out = a.sl_out + out_row * k;
+      if (n > k) {
+        int n2 = 1;
+        while (n2 < n) n2 <<= 1;
+        for (int x = n + threadIdx.x; x < n2; x += NT) bb[x] = EMPTY;
+        block_bitonic_sort(bb, n2);
+      }
+      for (int r = threadIdx.x; r < k; r += NT) out[r] = r < n ? bb[r] : EMPTY;
+      continue;
+    } else {
     // final: the entries within the block threshold are gathered into the table
     // area (it holds every buffer), cut near the k best distances, given their
     // ids (read only here) and ranked exactly by (distance, id)
@@ -1003,6 +1159,7 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
     for (int r = m + threadIdx.x; r < k; r += NT) {
       o_ids[r] = -1;
       o_dists[r] = __int_as_float(0x7f800000);
+    }
     }
   }
 }
@@ -1122,24 +1279,47 @@ __global__ void __launch_bounds__(256) rescore_kernel(RescoreArgs r) {
     }
     __syncthreads();
     const float* lut = r.lut + q * M * KSUB;
-    for (int e = threadIdx.x; e < r.S; e += NT) {
-      const uint64_t s = r.sl[q * r.S + e];
-      if (s == EMPTY) continue;
-      const uint32_t pos = (uint32_t)s;
-      uint32_t lo = 0, hi = ncell;  // last cell with offsets[cell] <= pos
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(r.offsets + mid) <= pos) lo = mid; else hi = mid;
-      }
-      const uint32_t i = lo / (uint32_t)r.T, j = lo % (uint32_t)r.T;
-      const float key = __fadd_rn(r.d1[q * r.T + i], r.d2[q * r.T + j]);
-      Code<M> code;
-      code.load(r.codes, pos);
-      float part = __ldg(r.cross + pos);
+    // four shortlisted positions per thread at a time: their binary searches for
+    // the cell (the last cell with offsets[cell] <= pos) run in lockstep, so the
+    // dependent loads of the four overlap
+    constexpr int G = 4;
+    for (int e0 = threadIdx.x; e0 < r.S; e0 += G * NT) {
+      uint32_t pos[G], lo[G], hi[G];
+      bool ok[G];
 #pragma unroll
-      for (int kk = 0; kk < M; ++kk) part += __ldg(lut + kk * KSUB + code.byte(kk));
-      const float dist = key + part;
-      tk.buf[atomicAdd(&nbuf, 1)] = ((uint64_t)f2ord(dist) << 32) | (uint32_t)__ldg(r.ids + pos);
+      for (int g = 0; g < G; ++g) {
+        const int e = e0 + g * NT;
+        const uint64_t s = e < r.S ? r.sl[q * r.S + e] : EMPTY;
+        ok[g] = s != EMPTY;
+        pos[g] = (uint32_t)s;
+        lo[g] = 0;
+        hi[g] = ok[g] ? ncell : 1u;
+      }
+      for (int step = 0; step < 32; ++step) {  // ncell <= 2^32: at most 32 halvings
+        bool more = false;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          if (hi[g] - lo[g] > 1) {
+            const uint32_t mid = lo[g] + ((hi[g] - lo[g]) >> 1);
+            if (__ldg(r.offsets + mid) <= pos[g]) lo[g] = mid; else hi[g] = mid;
+            more = true;
+          }
+        }
+        if (!more) break;
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        if (!ok[g]) continue;
+        const uint32_t i = lo[g] / (uint32_t)r.T, j = lo[g] % (uint32_t)r.T;
+        const float key = __fadd_rn(r.d1[q * r.T + i], r.d2[q * r.T + j]);
+        Code<M> code;
+        code.load(r.codes, pos[g]);
+        float part = __ldg(r.cross + pos[g]);
+#pragma unroll
+        for (int kk = 0; kk < M; ++kk) part += __ldg(lut + kk * KSUB + code.byte(kk));
+        const float dist = key + part;
+        tk.buf[atomicAdd(&nbuf, 1)] = ((uint64_t)f2ord(dist) << 32) | (uint32_t)__ldg(r.ids + pos[g]);
+      }
     }
     __syncthreads();
     block_topk_finish<NT>(tk, r.k, r.out_ids + q * r.k, r.out_dists + q * r.k);
@@ -1296,13 +1476,14 @@ void run_fbpq_cfg(const ScanArgs& a, cudaStream_t st) {
   check_launch("fbpq scan kernel");
 }
 
-template <int M, int NT, int D, int U, int KW, int CH, bool HB, bool WQ>
+template <int M, int NT, int D, int U, int KW, int CH, bool HB, bool WQ, int RV = FB_POINT, int BBC = 0>
 void run_fbpq_seg_t(const ScanArgs& a, cudaStream_t st) {
   constexpr int NW = NT / 32;
-  const size_t smem = (HB ? (size_t)4 * (MAX_T / 32) * 4 : (size_t)M * KSUB * 4) +
-                      (size_t)NW * KW * 8 + (size_t)NW * 256 * 4 + (size_t)CH * 8 + (size_t)(CH + 2) * 4 +
-                      (HB ? (size_t)CH * 8 : 0);
-  auto kern = fbpq_scan_seg_kernel<M, NT, D, U, KW, CH, HB, WQ>;
+  constexpr size_t TAB = (size_t)M * KSUB * (RV == FB_Q8 ? 1 : (RV == FB_F16 ? 2 : 4));
+  const size_t smem = (HB ? (size_t)4 * (MAX_T / 32) * 4 : TAB) + (size_t)NW * KW * 8 +
+                      (BBC ? 0 : (size_t)NW * 256 * 4) + (size_t)CH * 8 + (size_t)(CH + 2) * 4 +
+                      (HB ? (size_t)CH * 8 : 0) + (size_t)BBC * 8;
+  auto kern = fbpq_scan_seg_kernel<M, NT, D, U, KW, CH, HB, WQ, RV, BBC>;
   BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // HB reads its tables through L1: shared memory for five CTAs (132 KB), the rest as cache
   if (HB) BPQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 57));
@@ -1323,7 +1504,8 @@ void run_fbpq_seg_t(const ScanArgs& a, cudaStream_t st) {
     check_launch("partial list merge kernel");
     return;
   }
-  const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
+  // a selected list (its length is on the device): a few CTAs per SM, those past its end exit
+  const int grid = (int)std::min<int64_t>(a.nq, a.sel ? (int64_t)8 * a.sm_count : (int64_t)1 << 20);
   kern<<<grid, NT, smem, st>>>(a);
   check_launch("fbpq segment scan kernel");
 }
@@ -1409,10 +1591,20 @@ void launch_scan_reduced(const ScanArgs& a, bool f16, cudaStream_t st) {
   BPQ_CHECK(a.k >= 1 && a.k <= MAX_K, BPQ_EINVAL, "shortlist must be in [1, 1024]");
   BPQ_CHECK(a.D == 128 && (a.M == 8 || a.M == 16), BPQ_EINVAL,
             "the reduced-precision scan is built for D = 128, M = 8 or 16");
-  if (a.M == 8 && f16) run_fbpq<8, FB_F16>(a, st);
-  else if (a.M == 8) run_fbpq<8, FB_Q8>(a, st);
-  else if (f16) run_fbpq<16, FB_F16>(a, st);
-  else run_fbpq<16, FB_Q8>(a, st);
+  BPQ_CHECK(a.sl_out && a.lut_scale && (f16 ? a.lut16 != nullptr : a.lut8 != nullptr), BPQ_EINVAL,
+            "shortlist scan: missing table or output");
+  // a block buffer of 768 entries for shortlists up to 480 (eight CTAs per SM), else 2048
+  if (a.k <= 480) {
+    if (a.M == 8 && f16) run_fbpq_seg_t<8, 128, 1, 4, 256, 512, false, false, FB_F16, 768>(a, st);
+    else if (a.M == 8) run_fbpq_seg_t<8, 128, 1, 4, 256, 512, false, false, FB_Q8, 768>(a, st);
+    else if (f16) run_fbpq_seg_t<16, 128, 1, 4, 256, 512, false, false, FB_F16, 768>(a, st);
+    else run_fbpq_seg_t<16, 128, 1, 4, 256, 512, false, false, FB_Q8, 768>(a, st);
+  } else {
+    if (a.M == 8 && f16) run_fbpq_seg_t<8, 128, 1, 4, 256, 512, false, false, FB_F16, 2048>(a, st);
+    else if (a.M == 8) run_fbpq_seg_t<8, 128, 1, 4, 256, 512, false, false, FB_Q8, 2048>(a, st);
+    else if (f16) run_fbpq_seg_t<16, 128, 1, 4, 256, 512, false, false, FB_F16, 2048>(a, st);
+    else run_fbpq_seg_t<16, 128, 1, 4, 256, 512, false, false, FB_Q8, 2048>(a, st);
+  }
 }
 
 void launch_rescore(const RescoreArgs& r, cudaStream_t st) {

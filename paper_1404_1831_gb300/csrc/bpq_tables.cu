@@ -79,19 +79,47 @@ __global__ void __launch_bounds__(128) tc_table_kernel(const float* __restrict__
   unsigned char* sA3 = sA2 + TC_M * kpad * 2;
   unsigned char* sB2 = split ? sA3 + TC_M * kpad * 2 : sA2;  // second plane of B (when `bsplit`)
   int bad = 0;
-  for (int e = tid; e < TC_M * kpad; e += 128) {
-    const int r = e / kpad, k = e - r * kpad;
-    const float v = (a0 + r < na && k < pr.dim) ? A[(int64_t)(a0 + r) * lda + pr.a_off + k] : 0.f;
-    const __nv_bfloat16 b = __float2bfloat16_rn(v);
-    const bool inexact = __bfloat162float(b) != v;
-    bad |= inexact;
-    *reinterpret_cast<__nv_bfloat16*>(sA + core_off(r, k, KB)) = b;
+  // query slices, four values per step (float4 loads when aligned; kpad is a
+  // multiple of 16): the BF16 value, and with `split` the next two planes
+  const bool vec4 = ((pr.dim | lda | pr.a_off) & 3) == 0;
+  const int q4 = kpad >> 2;
+  for (int e = tid; e < TC_M * q4; e += 128) {
+    const int r = e / q4, k = (e - r * q4) << 2;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (a0 + r < na) {
+      const float* src = A + (int64_t)(a0 + r) * lda + pr.a_off + k;
+      if (vec4) {
+        if (k < pr.dim) {
+          const float4 f = *reinterpret_cast<const float4*>(src);
+          v[0] = f.x;
+          v[1] = f.y;
+          v[2] = f.z;
+          v[3] = f.w;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = k + j < pr.dim ? src[j] : 0.f;
+      }
+    }
+    __nv_bfloat16 b1[4], b2[4], b3[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      b1[j] = __float2bfloat16_rn(v[j]);
+      const float r1 = __fsub_rn(v[j], __bfloat162float(b1[j]));
+      bad |= r1 != 0.f;
+      b2[j] = __float2bfloat16_rn(r1);
+      b3[j] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(b2[j])));
+    }
+    auto pack = [](const __nv_bfloat16* b) {
+      uint2 pk;
+      pk.x = (uint32_t)__bfloat16_as_ushort(b[0]) | ((uint32_t)__bfloat16_as_ushort(b[1]) << 16);
+      pk.y = (uint32_t)__bfloat16_as_ushort(b[2]) | ((uint32_t)__bfloat16_as_ushort(b[3]) << 16);
+      return pk;
+    };
+    *reinterpret_cast<uint2*>(sA + core_off(r, k, KB)) = pack(b1);
     if (split) {
-      const float r1 = __fsub_rn(v, __bfloat162float(b));
-      const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
-      const __nv_bfloat16 b3 = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(b2)));
-      *reinterpret_cast<__nv_bfloat16*>(sA2 + core_off(r, k, KB)) = b2;
-      *reinterpret_cast<__nv_bfloat16*>(sA3 + core_off(r, k, KB)) = b3;
+      *reinterpret_cast<uint2*>(sA2 + core_off(r, k, KB)) = pack(b2);
+      *reinterpret_cast<uint2*>(sA3 + core_off(r, k, KB)) = pack(b3);
     }
   }
   const int bpl = (pr.b_planes == 2 && !bsplit) ? 0 : pr.b_planes;  // a second plane needs its smem

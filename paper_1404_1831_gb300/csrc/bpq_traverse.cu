@@ -335,7 +335,8 @@ __host__ __device__ inline Layout smem_layout(int T) {
 }
 
 // The general path: one CTA per query.  With only_marked, it takes only the
-// queries the warp kernel could not finish (ncells == FALLBACK).
+// queries the warp kernel could not finish (ncells == FALLBACK), from the warp
+// kernel's list when it kept one.
 constexpr int FALLBACK = -2;
 
 __global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a, int only_marked) {
@@ -371,8 +372,11 @@ __global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a, int onl
   // d2 ord keys live in a copy outside the union while the prefix is built
   uint32_t* dk = afk;
 
-  for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
-    if (only_marked && a.ncells[q] != FALLBACK) continue;  // uniform across the CTA
+  const bool listed = only_marked && a.fb_list;
+  const int64_t n_units = listed ? (int64_t)*a.fb_n : a.nq;
+  for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const int64_t q = listed ? (int64_t)a.fb_list[u] : u;
+    if (only_marked && !listed && a.ncells[q] != FALLBACK) continue;  // uniform across the CTA
     const int64_t L = a.L ? (int64_t)a.L[q] : (int64_t)a.L_scalar;
     const float* d1 = a.d1 + q * T;
     const float* d2 = a.d2 + q * T;
@@ -917,6 +921,15 @@ __device__ __noinline__ bool build_grid(WarpSmem& W, const float* d1, const floa
   return true;
 }
 
+// A query the warp kernel cannot finish: marked for the CTA kernel (and listed).
+__device__ __forceinline__ void hand_over(const TraverseArgs& a, int64_t q) {
+  a.ncells[q] = FALLBACK;
+  if (a.fb_list) {
+    a.handed[q] = 1;
+    a.fb_list[atomicAdd(a.fb_n, 1)] = (int32_t)q;
+  }
+}
+
 __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs a) {
   __shared__ WarpSmem smw[WPB];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -936,7 +949,7 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
     long long pcnt = 0;
     const float want_max = 0.9f * (float)PCAP;
     if (want > want_max && T > PCAP) {
-      if (lane == 0) a.ncells[q] = FALLBACK;
+      if (lane == 0) hand_over(a, q);
       continue;
     }
     __syncwarp();
@@ -1178,8 +1191,9 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
     }
     if (lane == 0) {
       if (fb) {
-        a.ncells[q] = FALLBACK;
+        hand_over(a, q);
       } else {
+        if (a.handed) a.handed[q] = 0;
         a.ncells[q] = overflow ? -1 : nout;
         a.npoints[q] = committed;
         if (overflow) atomicOr(a.status, STATUS_OVERFLOW);
@@ -1192,8 +1206,8 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
 
 int traverse_band_capacity() { return ECAP; }
 
-void launch_traverse(const TraverseArgs& a, cudaStream_t st) {
-  if (a.nq <= 0) return;
+bool launch_traverse_warp(const TraverseArgs& a, cudaStream_t st) {
+  if (a.nq <= 0) return false;
   BPQ_CHECK(a.T >= 1 && a.T <= MAX_T, BPQ_EINVAL, "T out of range for the traversal");
   const size_t smem = smem_layout(a.T).total;
   BPQ_CHECK(smem <= 227 * 1024, BPQ_EINVAL, "T too large for the traversal's shared memory");
@@ -1202,15 +1216,65 @@ void launch_traverse(const TraverseArgs& a, cudaStream_t st) {
     const int grid = (int)std::min<int64_t>(a.nq, 1 << 20);
     traverse_kernel<<<grid, NT, smem, st>>>(a, 0);
     check_launch("traverse kernel");
-    return;
+    return false;
   }
-  // common path: one warp per query; then the queries it marked, one CTA each
+  // common path: one warp per query
   const int wgrid = (int)std::min<int64_t>((a.nq + WPB - 1) / WPB, 1 << 20);
   traverse_warp_kernel<<<wgrid, WPB * 32, 0, st>>>(a);
   check_launch("traverse warp kernel");
+  return true;
+}
+
+// The queries the warp kernel marked, one CTA each (from its list when it kept
+// one: the CTAs past the list's end exit at once).
+void launch_traverse_marked(const TraverseArgs& a, cudaStream_t st) {
+  const size_t smem = smem_layout(a.T).total;
   const int grid = (int)std::min<int64_t>(a.nq, 4096);
   traverse_kernel<<<grid, NT, smem, st>>>(a, 1);
   check_launch("traverse kernel");
+}
+
+void launch_traverse(const TraverseArgs& a, cudaStream_t st) {
+  if (launch_traverse_warp(a, st)) launch_traverse_marked(a, st);
+}
+
+namespace {
+
+// One warp per query: in-place, order-keeping compaction of the visited cells
+// with the shard's begin and count (a step's 32 records are read before any of
+// them is overwritten; writes go at or below the read positions).
+__global__ void __launch_bounds__(256) localize_cells_kernel(TraverseArgs a, const uint32_t* __restrict__ loff) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (q >= a.nq) return;
+  const int n = a.ncells[q];
+  if (n <= 0) return;  // empty, or an overflow (-1) that the status word reports
+  bpq_cell* cl = a.cells + q * (int64_t)a.cap;
+  int kept = 0;
+  for (int e0 = 0; e0 < n; e0 += 32) {
+    const int e = e0 + lane;
+    bpq_cell c{};
+    bool keep = false;
+    if (e < n) {
+      c = cl[e];
+      c.begin = __ldg(loff + c.cell);
+      c.count = __ldg(loff + c.cell + 1) - c.begin;
+      keep = c.count > 0;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    __syncwarp();
+    if (keep) cl[kept + __popc(m & lanemask_lt())] = c;
+    kept += __popc(m);
+  }
+  if (lane == 0) a.ncells[q] = kept;
+}
+
+}  // namespace
+
+void launch_localize_cells(const TraverseArgs& a, const uint32_t* loff, cudaStream_t st) {
+  if (a.nq <= 0) return;
+  localize_cells_kernel<<<(unsigned)((a.nq + 7) / 8), 256, 0, st>>>(a, loff);
+  check_launch("cell localization kernel");
 }
 
 }  // namespace bpq

@@ -49,6 +49,16 @@ def merge_topk(ids, dists, k: int):
     return out_i, out_d
 
 
+def global_cell_counts(local_counts, device=None, group=None):
+    """The whole index's per-cell counts: the sum over the point shards of each rank's
+    counts (numpy int64, T*T), by one all-reduce; every rank gets the same array."""
+    import torch
+    import torch.distributed as dist
+    t = torch.as_tensor(np.ascontiguousarray(local_counts, dtype=np.int64), device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return t.cpu().numpy()
+
+
 def gather_merge(ids, dists, k: int, group=None):
     """All-gather every rank's (nq, k) lists (torch tensors on the backend's device)
     and merge them on every rank.  Returns numpy (ids, dists)."""

@@ -121,3 +121,20 @@ def test_full_batch_equals_small_batches(full):
     parts = [full["ix"].search(full["q"][i:i + 2000], 10_000, 100, "fbpq") for i in range(0, full["q"].shape[0], 2000)]
     b = [torch.cat([p[j] for p in parts]).cpu().numpy() for j in range(2)]
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("L", [10_000, 100_000])
+def test_full_overlapped_passes_equal_separate_calls(full, L):
+    """bpq_search scans the queries the traversal's warp pass finished while, on a second
+    stream, the CTA pass takes the queries handed over to it (about 7 % at L = 10k, all at
+    L = 100k) and then scans them; every query's list equals the one of the separate
+    traversal and scan calls, which run one pass after the other."""
+    ix, q = full["ix"], full["q"][:4000]
+    ids, dists = ix.search(q, L, 100, "fbpq")
+    ix.search_status()
+    cap = int(min(L, ix.info().n_nonempty))
+    _, _, lut = ix.query_tables(q)
+    cells, ncells, _ = ix.traverse(q, L, cap)
+    ids2, dists2 = ix.scan(q, lut, cells, ncells, 100, "fbpq")
+    assert np.array_equal(ids.cpu().numpy(), ids2.cpu().numpy())
+    assert np.array_equal(dists.cpu().numpy(), dists2.cpu().numpy())

@@ -3,11 +3,13 @@
 * 1B points (T = 1024, M = 8, the serving configuration): the GPU trains the
   codebooks and builds the index; the oracle takes the codebooks as given, checks
   the lists by re-encoding 20,000 sampled points (Eqs. 6-7), and searches the
-  GPU's lists (copied to host memory) for sampled queries of a 10k-query batch at
-  L = 1k and 10k: identical top-100 ids and distances.
+  GPU's lists (copied to host memory) for 1,000 randomly sampled queries of a
+  10k-query batch at L = 1k and 10k (multi-sequence traversal; a few of them also
+  with the full-sort definition): identical top-100 ids and distances, hence
+  identical recall.
 * 100M points with M = 16 (the precision configuration): the int8 and FP16 table
   shortlists (1000, exact re-score) and the FP32 search equal the oracle's on
-  sampled queries at L = 30k.
+  200 sampled queries at L = 30k.
 """
 import numpy as np
 import pytest
@@ -16,7 +18,8 @@ from tests.parity import assert_topk_match
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
-SAMPLE = (0, 1, 17, 999, 4242, 9999)
+SAMPLE = (0, 1, 17, 999, 4242, 9999)  # also checked against the full-sort traversal
+BULK = tuple(sorted(np.random.default_rng(5).choice(10_000, 1_000, replace=False).tolist()))
 
 
 def build(w, variant="global"):
@@ -42,7 +45,7 @@ def build(w, variant="global"):
     oix = O.OracleIndex(cb=cb, lists=lists, variant="global", tables=O.fbpq_tables(cb))
     q = sdev.points_cuda(mix, sd.STREAM_QUERY, 0, w.n_query)
     torch.cuda.synchronize()
-    return dict(w=w, mix=mix, ix=ix, oix=oix, q=q, qh=sd.points(mix, sd.STREAM_QUERY, 0, max(SAMPLE) + 1))
+    return dict(w=w, mix=mix, ix=ix, oix=oix, q=q, qh=sd.points(mix, sd.STREAM_QUERY, 0, w.n_query))
 
 
 @pytest.fixture(scope="module")
@@ -86,6 +89,11 @@ def test_1b_search_sampled(one_b, L):
         o_ids, o_d, _, _ = O.search_one(one_b["oix"], one_b["qh"][n], L, k, "fbpq", traversal="full_sort")
         exact += assert_topk_match(ids[n:n + 1], dists[n:n + 1], o_ids[None], o_d[None])
     assert exact == len(SAMPLE)
+    exact = 0
+    for n in BULK:
+        o_ids, o_d, _, _ = O.search_one(one_b["oix"], one_b["qh"][n], L, k, "fbpq")
+        exact += assert_topk_match(ids[n:n + 1], dists[n:n + 1], o_ids[None], o_d[None])
+    assert exact == len(BULK)  # bit-identical lists on every sampled query
 
 
 @pytest.fixture(scope="module")
@@ -113,10 +121,11 @@ def test_100m_m16_shortlists_sampled(c3, precision):
         ids, dists = c3["ix"].search_shortlist(c3["q"], L, k, shortlist=S, precision=precision)
     ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
     exact = 0
-    for n in SAMPLE:
+    picks = SAMPLE + BULK[::5]
+    for n in picks:
         if precision == "fp32":
-            o_ids, o_d, _, _ = O.search_one(c3["oix"], c3["qh"][n], L, k, "fbpq", traversal="full_sort")
+            o_ids, o_d, _, _ = O.search_one(c3["oix"], c3["qh"][n], L, k, "fbpq")
         else:
             o_ids, o_d = O.search_shortlist_one(c3["oix"], c3["qh"][n], L, k, S, precision)
         exact += assert_topk_match(ids[n:n + 1], dists[n:n + 1], o_ids[None], o_d[None])
-    assert exact == len(SAMPLE)
+    assert exact == len(picks)

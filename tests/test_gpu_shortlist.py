@@ -91,3 +91,27 @@ def test_shortlist_rejects_bad_arguments(m8):
     for k, S in ((100, 50), (10, 1025), (0, 10)):
         with pytest.raises(bpq.BpqError):
             m8["ix"].search_shortlist(m8["q"][:2], 1000, k, shortlist=S)
+
+
+@pytest.mark.parametrize("precision", ["int8", "fp16"])
+def test_shortlist_cut_inside_a_large_tie_group(tiny_oracle, precision):
+    """4000 copies of one point under distinct ids share a cell, a code and a score: a
+    shortlist of 1000 is cut inside that tie group, by list position as in the oracle
+    (the group is larger than the scan's block buffer keeps by score alone)."""
+    import paper_1404_1831_gb300 as bpq
+    cb = tiny_oracle["cb"]
+    base = tiny_oracle["base"][:6000]
+    X = np.concatenate([base, np.repeat(base[:1], 4000, axis=0)])
+    ids = np.arange(len(X), dtype=np.int32)
+    oix = O.build_index(cb, X, ids=ids)
+    ix = bpq.Index.create(cb.C1, cb.C2, cb.R)
+    ix.add(torch.as_tensor(X, dtype=torch.float32, device=DEV), ids=torch.as_tensor(ids, device=DEV))
+    ix.finalize()
+    qn = np.concatenate([base[:1].astype(np.float64), base[:1] + 0.5, tiny_oracle["queries"][:2]])
+    q = torch.as_tensor(qn, dtype=torch.float32, device=DEV)
+    g_ids, g_d = [t.cpu().numpy() for t in ix.search_shortlist(q, 5000, 100, shortlist=1000, precision=precision)]
+    o_ids, o_d = O.search_shortlist(oix, qn, 5000, 100, 1000, precision)
+    assert np.array_equal(g_ids, o_ids)
+    assert np.array_equal(g_d.astype(np.float64), o_d)
+    copies = np.r_[0, 6000:10000]  # base[0] and its copies
+    assert np.isin(g_ids[0], copies).sum() >= 90  # the tie group fills the first answer

@@ -63,16 +63,19 @@ def _worker(rank, world, port, out_dir):
         full = O.build_index(cb, base)
         start, count = multi.shard_points(len(base), rank, world)
         shard = O.build_index(cb, base[start:start + count], ids=np.arange(start, start + count))
+        # the whole index's counts, summed over the shards by one all-reduce
+        gcounts = multi.global_cell_counts(shard.lists.counts())
         k = 30
         ids = np.empty((len(queries), k), dtype=np.int64)
         dd = np.empty((len(queries), k))
         for n, q in enumerate(queries):
             ids[n], dd[n], _, _ = O.search_one(shard, q, 2000, k, "fbpq", traversal="full_sort",
-                                               cut_counts=full.lists.counts())
+                                               cut_counts=gcounts)
         mi, md = multi.gather_merge(torch.as_tensor(ids), torch.as_tensor(dd), k)
         if rank == 0:
             ref_i, ref_d, _ = O.search(full, queries, 2000, k, "fbpq", traversal="full_sort")
-            np.savez(os.path.join(out_dir, "r.npz"), mi=mi, md=md, ri=ref_i, rd=ref_d, mx=mx)
+            np.savez(os.path.join(out_dir, "r.npz"), mi=mi, md=md, ri=ref_i, rd=ref_d, mx=mx,
+                     gc=np.array_equal(gcounts, full.lists.counts()))
     finally:
         dist.destroy_process_group()
 
@@ -82,4 +85,5 @@ def test_sharded_search_merges_to_single_index_answer(tmp_path):
     tmp.spawn(_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
     r = np.load(tmp_path / "r.npz")
     assert float(r["mx"]) == 2.5
+    assert bool(r["gc"])  # summed shard counts = the single index's counts
     assert np.array_equal(r["mi"], r["ri"]) and np.array_equal(r["md"], r["rd"])
