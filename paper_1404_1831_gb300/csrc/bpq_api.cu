@@ -301,7 +301,7 @@ namespace {
 // the fork and join events; created on first use and kept for the process.
 struct AuxStream {
   cudaStream_t s = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, lut = nullptr;
   std::mutex m;  // one caller at a time enqueues the fork ... join sequence
 };
 
@@ -320,6 +320,7 @@ AuxStream* aux_stream(cudaStream_t st) {
   BPQ_CUDA(cudaStreamCreateWithFlags(&a->s, cudaStreamNonBlocking));
   BPQ_CUDA(cudaEventCreateWithFlags(&a->fork, cudaEventDisableTiming));
   BPQ_CUDA(cudaEventCreateWithFlags(&a->join, cudaEventDisableTiming));
+  BPQ_CUDA(cudaEventCreateWithFlags(&a->lut, cudaEventDisableTiming));
   AuxStream* r = a.get();
   pool.emplace(std::make_pair(dev, st), std::move(a));
   return r;
@@ -522,7 +523,7 @@ namespace {
 // ---------------------------------------------------------------------------
 struct ShortlistLayout {
   Layout base;
-  size_t lutr, scale, sl, total;
+  size_t lutr, scale, sl, hint, total;
 };
 
 ShortlistLayout shortlist_layout(const bpq_index& ix, int64_t nq, int64_t L_max, int S) {
@@ -535,6 +536,8 @@ ShortlistLayout shortlist_layout(const bpq_index& ix, int64_t nq, int64_t L_max,
   o = align_up(o + (size_t)nq * 4);
   l.sl = o;
   o = align_up(o + (size_t)nq * S * 8);
+  l.hint = o;
+  o = align_up(o + position_hint_count(ix.n_points) * 4);
   l.total = o;
   return l;
 }
@@ -563,6 +566,9 @@ void run_shortlist(const bpq_index& ix, const float* q, int64_t nq, const int64_
   char* w = static_cast<char*>(ws);
   BPQ_CUDA(cudaMemsetAsync(w + l.base.status, 0, 4, st));
   const float rho = traversal_rho(ix);
+  // the re-score's cell hints of the list positions (every chunk uses them)
+  launch_position_hints(ix.offsets.as<uint32_t>(), (int64_t)ix.p.T * ix.p.T, ix.n_points,
+                        reinterpret_cast<uint32_t*>(w + l.hint), st);
   for (int64_t c0 = 0; c0 < nq; c0 += chunk) {
     const int64_t nc = std::min(chunk, nq - c0);
     const float* qc = q + c0 * ix.p.D;
@@ -624,6 +630,7 @@ void run_shortlist(const bpq_index& ix, const float* q, int64_t nq, const int64_
     r.d2 = d2;
     r.lut = lut;
     r.offsets = ix.offsets.as<uint32_t>();
+    r.hint = reinterpret_cast<const uint32_t*>(w + l.hint);
     r.codes = ix.codes.as<uint8_t>();
     r.cross = ix.cross.as<float>();
     r.ids = ix.ids.as<int32_t>();

@@ -397,6 +397,7 @@ struct RescoreArgs {
   const float* d2;
   const float* lut;       // nq x M x 256 (FP32)
   const uint32_t* offsets;  // T*T + 1
+  const uint32_t* hint;     // position_hints: the cell of every 256th list position
   const uint8_t* codes;
   const float* cross;
   const int32_t* ids;
@@ -404,6 +405,10 @@ struct RescoreArgs {
   float* out_dists;
 };
 void launch_rescore(const RescoreArgs& r, cudaStream_t st);
+// hint[b] = the cell holding list position min(256 b, n - 1), b = 0 .. ceil(n / 256):
+// the cell of position p then lies in [hint[p / 256], hint[p / 256 + 1]].
+size_t position_hint_count(int64_t n_points);
+void launch_position_hints(const uint32_t* offsets, int64_t ncells, int64_t n_points, uint32_t* hint, cudaStream_t st);
 // Per-query reduced-precision table and step from the FP32 table (bpq_search_shortlist step 1).
 // out: nq x M x 256 uint8 (int8 form) or FP16 bits (fp16 form).
 void launch_quant_lut(const float* lut, int M, int64_t nq, void* out, float* scale, bool f16, cudaStream_t st);

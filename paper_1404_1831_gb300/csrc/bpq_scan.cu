@@ -822,12 +822,15 @@ __device__ void sl_flush(const uint64_t* wb, int wn, int S, uint64_t* bb, int* b
 // >= S + 32; a small one for short shortlists keeps eight CTAs per SM); the S best
 // composites go to a.sl_out in any order.
 template <int M, int NT, int D, int U, int KW, int CH, bool HB, bool WQ, int RV, int BBC>
-__global__ void __launch_bounds__(NT, (HB || BBC > 1024) ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs a) {
+__global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs a) {
   constexpr int NW = NT / 32, R = CH / NT, M2 = M / 2;
   constexpr bool RED = RV == FB_Q8 || RV == FB_F16;
-  static_assert(CH % NT == 0 && KW == 256, "shape (the exact prune keeps its payloads in the warp's 256 counters)");
+  static_assert(CH % NT == 0 && (KW == 256 || (RED && KW >= 64)),
+                "shape (the exact prune keeps its payloads in the warp's 256 counters)");
   static_assert(RV == FB_POINT || (RED && !HB && !WQ && BBC > KW), "variant");
   static_assert(RED || BBC == 0, "the block buffer is the shortlists'");
+  // the final sort pads the at most BBC - KW entries to the next power of two in place
+  static_assert(BBC == 0 || (BBC & (BBC - 1)) == 0, "the block buffer's size is a power of two");
   // the query's table: FP32 (FBPQ), int8 or FP16 (shortlists); none (HB)
   constexpr int AREA0 = HB ? 0 : M * KSUB * (RV == FB_Q8 ? 1 : (RV == FB_F16 ? 2 : 4));
   constexpr int TWMAX = MAX_T / 32;
@@ -1263,27 +1266,20 @@ __global__ void __launch_bounds__(256) merge_parts_kernel(ScanArgs a) {
 // ---------------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(256) rescore_kernel(RescoreArgs r) {
-  constexpr int NT = 256;
-  using TK = BlockTopK<NT>;
-  __shared__ uint64_t bufs[2 * TK::CAP];
-  __shared__ unsigned long long thr;
-  __shared__ int nbuf;
-  __shared__ uint32_t hist[260];
-  const uint32_t ncell = (uint32_t)r.T * (uint32_t)r.T;
+  constexpr int NT = 256, G = 4;
+  __shared__ __align__(16) float lut[M * KSUB];
+  __shared__ uint64_t buf[MAX_K];
+  int n2 = 1;
+  while (n2 < r.S) n2 <<= 1;
   for (int64_t q = blockIdx.x; q < r.nq; q += gridDim.x) {
+    __syncthreads();  // the previous query's list is written out
+    const float4* src = reinterpret_cast<const float4*>(r.lut + q * M * KSUB);
+    for (int t = threadIdx.x; t < M * KSUB / 4; t += NT) reinterpret_cast<float4*>(lut)[t] = src[t];
     __syncthreads();
-    TK tk{bufs, bufs + TK::CAP, &nbuf, &thr, hist};
-    if (threadIdx.x == 0) {
-      thr = EMPTY;
-      nbuf = 0;
-    }
-    __syncthreads();
-    const float* lut = r.lut + q * M * KSUB;
-    // four shortlisted positions per thread at a time: their binary searches for
-    // the cell (the last cell with offsets[cell] <= pos) run in lockstep, so the
-    // dependent loads of the four overlap
-    constexpr int G = 4;
-    for (int e0 = threadIdx.x; e0 < r.S; e0 += G * NT) {
+    // four shortlisted positions per thread at a time; the cell of each (the last
+    // cell with offsets[cell] <= pos) is searched between the two hints around it,
+    // the four searches in lockstep so that their dependent loads overlap
+    for (int e0 = threadIdx.x; e0 < n2; e0 += G * NT) {
       uint32_t pos[G], lo[G], hi[G];
       bool ok[G];
 #pragma unroll
@@ -1292,10 +1288,10 @@ __global__ void __launch_bounds__(256) rescore_kernel(RescoreArgs r) {
         const uint64_t s = e < r.S ? r.sl[q * r.S + e] : EMPTY;
         ok[g] = s != EMPTY;
         pos[g] = (uint32_t)s;
-        lo[g] = 0;
-        hi[g] = ok[g] ? ncell : 1u;
+        lo[g] = ok[g] ? __ldg(r.hint + (pos[g] >> 8)) : 0u;
+        hi[g] = ok[g] ? __ldg(r.hint + (pos[g] >> 8) + 1) + 1u : 1u;
       }
-      for (int step = 0; step < 32; ++step) {  // ncell <= 2^32: at most 32 halvings
+      for (int step = 0; step < 32; ++step) {
         bool more = false;
 #pragma unroll
         for (int g = 0; g < G; ++g) {
@@ -1309,21 +1305,43 @@ __global__ void __launch_bounds__(256) rescore_kernel(RescoreArgs r) {
       }
 #pragma unroll
       for (int g = 0; g < G; ++g) {
-        if (!ok[g]) continue;
-        const uint32_t i = lo[g] / (uint32_t)r.T, j = lo[g] % (uint32_t)r.T;
-        const float key = __fadd_rn(r.d1[q * r.T + i], r.d2[q * r.T + j]);
-        Code<M> code;
-        code.load(r.codes, pos[g]);
-        float part = __ldg(r.cross + pos[g]);
+        const int e = e0 + g * NT;
+        if (e >= n2) continue;
+        uint64_t x = EMPTY;
+        if (ok[g]) {
+          const uint32_t i = lo[g] / (uint32_t)r.T, j = lo[g] % (uint32_t)r.T;
+          const float key = __fadd_rn(r.d1[q * r.T + i], r.d2[q * r.T + j]);
+          Code<M> code;
+          code.load(r.codes, pos[g]);
+          float part = __ldg(r.cross + pos[g]);
 #pragma unroll
-        for (int kk = 0; kk < M; ++kk) part += __ldg(lut + kk * KSUB + code.byte(kk));
-        const float dist = key + part;
-        tk.buf[atomicAdd(&nbuf, 1)] = ((uint64_t)f2ord(dist) << 32) | (uint32_t)__ldg(r.ids + pos[g]);
+          for (int kk = 0; kk < M; ++kk) part += lut[kk * KSUB + code.byte(kk)];
+          x = ((uint64_t)f2ord(key + part) << 32) | (uint32_t)__ldg(r.ids + pos[g]);
+        }
+        buf[e] = x;
       }
     }
-    __syncthreads();
-    block_topk_finish<NT>(tk, r.k, r.out_ids + q * r.k, r.out_dists + q * r.k);
+    block_bitonic_sort(buf, n2);  // (distance, id) order; the padding sorts last
+    for (int t = threadIdx.x; t < r.k; t += NT) {
+      const uint64_t x = buf[t];
+      r.out_ids[q * r.k + t] = x == EMPTY ? -1 : (int32_t)(uint32_t)x;
+      r.out_dists[q * r.k + t] = x == EMPTY ? __int_as_float(0x7f800000) : ord2f((uint32_t)(x >> 32));
+    }
   }
+}
+
+// hint[b] = the last cell c with offsets[c] <= min(256 b, n - 1)
+__global__ void position_hint_kernel(const uint32_t* __restrict__ offsets, int64_t ncells, int64_t n,
+                                     int64_t nb, uint32_t* __restrict__ hint) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > nb) return;
+  const uint32_t x = (uint32_t)min(b * 256, n - 1);
+  int64_t lo = 0, hi = ncells;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (offsets[mid] <= x) lo = mid; else hi = mid;
+  }
+  hint[b] = (uint32_t)lo;
 }
 
 // ---------------------------------------------------------------------------
@@ -1593,18 +1611,29 @@ void launch_scan_reduced(const ScanArgs& a, bool f16, cudaStream_t st) {
             "the reduced-precision scan is built for D = 128, M = 8 or 16");
   BPQ_CHECK(a.sl_out && a.lut_scale && (f16 ? a.lut16 != nullptr : a.lut8 != nullptr), BPQ_EINVAL,
             "shortlist scan: missing table or output");
-  // a block buffer of 768 entries for shortlists up to 480 (eight CTAs per SM), else 2048
-  if (a.k <= 480) {
-    if (a.M == 8 && f16) run_fbpq_seg_t<8, 128, 1, 4, 256, 512, false, false, FB_F16, 768>(a, st);
-    else if (a.M == 8) run_fbpq_seg_t<8, 128, 1, 4, 256, 512, false, false, FB_Q8, 768>(a, st);
-    else if (f16) run_fbpq_seg_t<16, 128, 1, 4, 256, 512, false, false, FB_F16, 768>(a, st);
-    else run_fbpq_seg_t<16, 128, 1, 4, 256, 512, false, false, FB_Q8, 768>(a, st);
+  // warp buffers of 128, chunks of 256 cells and a block buffer of 1024 entries (shortlists
+  // up to 608) or 2048 keep the shared memory near 27 KB: eight CTAs per SM
+  if (a.k <= 608) {
+    if (a.M == 8 && f16) run_fbpq_seg_t<8, 128, 1, 4, 128, 256, false, false, FB_F16, 1024>(a, st);
+    else if (a.M == 8) run_fbpq_seg_t<8, 128, 1, 4, 128, 256, false, false, FB_Q8, 1024>(a, st);
+    else if (f16) run_fbpq_seg_t<16, 128, 1, 4, 128, 256, false, false, FB_F16, 1024>(a, st);
+    else run_fbpq_seg_t<16, 128, 1, 4, 128, 256, false, false, FB_Q8, 1024>(a, st);
   } else {
-    if (a.M == 8 && f16) run_fbpq_seg_t<8, 128, 1, 4, 256, 512, false, false, FB_F16, 2048>(a, st);
-    else if (a.M == 8) run_fbpq_seg_t<8, 128, 1, 4, 256, 512, false, false, FB_Q8, 2048>(a, st);
-    else if (f16) run_fbpq_seg_t<16, 128, 1, 4, 256, 512, false, false, FB_F16, 2048>(a, st);
-    else run_fbpq_seg_t<16, 128, 1, 4, 256, 512, false, false, FB_Q8, 2048>(a, st);
+    if (a.M == 8 && f16) run_fbpq_seg_t<8, 128, 1, 4, 128, 256, false, false, FB_F16, 2048>(a, st);
+    else if (a.M == 8) run_fbpq_seg_t<8, 128, 1, 4, 128, 256, false, false, FB_Q8, 2048>(a, st);
+    else if (f16) run_fbpq_seg_t<16, 128, 1, 4, 128, 256, false, false, FB_F16, 2048>(a, st);
+    else run_fbpq_seg_t<16, 128, 1, 4, 128, 256, false, false, FB_Q8, 2048>(a, st);
   }
+}
+
+size_t position_hint_count(int64_t n_points) { return (size_t)((n_points + 255) / 256) + 2; }
+
+void launch_position_hints(const uint32_t* offsets, int64_t ncells, int64_t n_points, uint32_t* hint,
+                           cudaStream_t st) {
+  if (n_points <= 0) return;
+  const int64_t nb = (n_points + 255) / 256;
+  position_hint_kernel<<<(unsigned)((nb + 256) / 256), 256, 0, st>>>(offsets, ncells, n_points, nb, hint);
+  check_launch("position hint kernel");
 }
 
 void launch_rescore(const RescoreArgs& r, cudaStream_t st) {
