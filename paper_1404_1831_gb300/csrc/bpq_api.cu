@@ -407,7 +407,22 @@ void bpq::run_queries(const bpq_index& ix, const float* q, int64_t nq, const int
       qcoarse = rc;
       qres = rr;
     }
-    launch_query_tables(ix, qcoarse, nc, d1, d2, lut, st, reinterpret_cast<int32_t*>(w + l.status), qres);
+    // FBPQ segment scan: the PQ table is built on the second stream beside the
+    // coarse tables and the traversal (only the scans read it)
+    AuxStream* aux = (scan && l.overlap) ? aux_stream(st) : nullptr;
+    std::unique_lock<std::mutex> aux_lock;  // held from the fork to the join
+    int32_t* status = reinterpret_cast<int32_t*>(w + l.status);
+    if (aux && lut) {
+      aux_lock = std::unique_lock<std::mutex>(aux->m);
+      BPQ_CUDA(cudaEventRecord(aux->fork, st));
+      BPQ_CUDA(cudaStreamWaitEvent(aux->s, aux->fork, 0));
+      launch_query_tables(ix, qcoarse, nc, nullptr, nullptr, lut, aux->s, status, qres);
+      BPQ_CUDA(cudaEventRecord(aux->lut, aux->s));
+      launch_query_tables(ix, qcoarse, nc, d1, d2, nullptr, st, status, qres);
+    } else {
+      aux = nullptr;
+      launch_query_tables(ix, qcoarse, nc, d1, d2, lut, st, status, qres);
+    }
     TraverseArgs ta{};
     ta.d1 = d1;
     ta.d2 = d2;
@@ -437,16 +452,15 @@ void bpq::run_queries(const bpq_index& ix, const float* q, int64_t nq, const int
     }
     ScanArgs sa = scan_args(ix, qres, nc, lut, ta.cells, ta.ncells, ta.cap, k, out_ids + c0 * k,
                             out_dists + c0 * k, reinterpret_cast<int32_t*>(w + l.qcounter));
-    AuxStream* aux = (scan && l.overlap) ? aux_stream(st) : nullptr;
     if (aux) {
       // the warp pass lists the queries it hands over; the CTA pass for them, then
-      // their scan, run on the second stream beside the scan of the other queries
+      // their scan, run on the second stream (after the PQ table) beside the scan
+      // of the other queries
       ta.fb_n = reinterpret_cast<int32_t*>(w + l.fb_n);
       ta.fb_list = reinterpret_cast<int32_t*>(w + l.fb_list);
       ta.handed = reinterpret_cast<uint8_t*>(w + l.fb_handed);
       BPQ_CUDA(cudaMemsetAsync(ta.fb_n, 0, 4, st));
       if (launch_traverse_warp(ta, st)) {
-        std::lock_guard<std::mutex> g(aux->m);
         BPQ_CUDA(cudaEventRecord(aux->fork, st));
         BPQ_CUDA(cudaStreamWaitEvent(aux->s, aux->fork, 0));
         launch_traverse_marked(ta, aux->s);
@@ -454,13 +468,16 @@ void bpq::run_queries(const bpq_index& ix, const float* q, int64_t nq, const int
         sb.sel = ta.fb_list;
         sb.sel_n = ta.fb_n;
         launch_scan(sb, scorer, aux->s);
+        BPQ_CUDA(cudaStreamWaitEvent(st, aux->lut, 0));
         sa.skip = ta.handed;
         launch_scan(sa, scorer, st);
         BPQ_CUDA(cudaEventRecord(aux->join, aux->s));
         BPQ_CUDA(cudaStreamWaitEvent(st, aux->join, 0));
       } else {
+        BPQ_CUDA(cudaStreamWaitEvent(st, aux->lut, 0));
         launch_scan(sa, scorer, st);  // the CTA pass took every query
       }
+      aux_lock.unlock();
       continue;
     }
     launch_traverse(ta, st);

@@ -692,10 +692,10 @@ __device__ uint32_t block_cut(const uint64_t* a, int n, int k, int* red) {
 // of a query.  S is up to 1024, more than a warp buffer holds, so the warps move
 // their buffered entries into one block buffer of BBC entries, one warp at a
 // time (a lock in shared memory); when it nears its capacity that warp cuts it
-// to the entries at or below a value v with at least S entries <= v (a count
-// bisection on the score bits over the buffer, stopped once S .. S + 32 remain)
-// and lowers the block threshold to (v, any position).  If a tie group at v
-// still fills the buffer, the cut is exact on the whole composite.
+// to the entries at or below a value v with at least S entries <= v (sl_cut_value:
+// a sampled guess checked by one count, else a count bisection) and lowers the
+// block threshold to (v, any position).  If a tie group at v still fills the
+// buffer, the cut is exact on the whole composite.
 
 // Entries of bb[0 .. n) with bits <= v kept in place (v on the whole composite
 // when `whole`, else on the score bits).  Warp-wide; returns the new count.
@@ -732,6 +732,85 @@ __device__ int sl_count(const uint64_t* bb, int n, uint32_t hi, bool hi_eq, long
   return warp_sum(c);
 }
 
+// Bitonic sort (ascending) of 256 keys held by one warp, eight per lane (element
+// lane * 8 + i in x[i]); pairs closer than 8 are in the same lane, farther pairs
+// are exchanged with shuffles.
+__device__ __forceinline__ void warp_sort256(uint32_t (&x)[8]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 256; size <<= 1) {
+#pragma unroll
+    for (int j = size >> 1; j > 0; j >>= 1) {
+      if (j < 8) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int p = i ^ j;
+          if (p > i) {
+            const bool up = (((lane * 8 + i) & size) == 0);
+            const uint32_t a = x[i], b = x[p];
+            const bool sw = (a > b) == up;
+            x[i] = sw ? b : a;
+            x[p] = sw ? a : b;
+          }
+        }
+      } else {
+        const int lj = j / 8;
+        const bool lower = (lane & lj) == 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const uint32_t o = __shfl_xor_sync(0xffffffffu, x[i], lj);
+          const bool up = (((lane * 8 + i) & size) == 0);
+          x[i] = (lower == up) ? min(x[i], o) : max(x[i], o);
+        }
+      }
+    }
+  }
+}
+
+// The cut of a full block buffer (n > S entries): a score value v with
+// S <= count(<= v) and, unless a tie group at v is larger, count(<= v) <= keep.
+// A guess from a sorted sample of 256 entries (aimed at S + 96 entries) is
+// checked with one count; a guess outside [S, keep] is refined by bisection
+// between it and the buffer's extreme.
+__device__ __noinline__ uint32_t sl_cut_value(const uint64_t* bb, int n, int S, int keep) {
+  const int lane = threadIdx.x & 31;
+  uint32_t x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = (uint32_t)(bb[(int)(((long long)(lane * 8 + i) * n) >> 8)] >> 32);
+  warp_sort256(x);
+  const int r = min(255, (int)(((long long)(S + 96) * 256 + n - 1) / n));
+  const uint32_t g = __shfl_sync(0xffffffffu, x[r & 7], r >> 3);
+  const int cg = sl_count(bb, n, g, false, 0xffffffffll);
+  if (cg >= S && cg <= keep) return g;
+  long long lo, hi;  // count(<= hi) >= S > count(<= lo)
+  if (cg < S) {
+    uint32_t mx = 0u;
+    for (int e = lane; e < n; e += 32) mx = max(mx, (uint32_t)(bb[e] >> 32));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    lo = g;
+    hi = mx;
+  } else {
+    uint32_t mn = 0xffffffffu;
+    for (int e = lane; e < n; e += 32) mn = min(mn, (uint32_t)(bb[e] >> 32));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    lo = (long long)mn - 1;
+    hi = g;
+  }
+  while (hi - lo > 1) {
+    const uint32_t mid = (uint32_t)(lo + ((hi - lo) >> 1));
+    const int c = sl_count(bb, n, mid, false, 0xffffffffll);
+    if (c >= S) {
+      hi = mid;
+      if (c <= keep) break;
+    } else {
+      lo = mid;
+    }
+  }
+  return (uint32_t)hi;
+}
+
 template <int KW, int BBC>
 __device__ void sl_flush(const uint64_t* wb, int wn, int S, uint64_t* bb, int* bb_n, int* lock,
                          unsigned long long* thr, int32_t* status) {
@@ -766,29 +845,8 @@ __device__ void sl_flush(const uint64_t* wb, int wn, int S, uint64_t* bb, int* b
   }
   __syncwarp();
   if (n > BBC - KW) {
-    uint32_t mn = 0xffffffffu, mx = 0u;
-    for (int e = lane; e < n; e += 32) {
-      const uint32_t h = (uint32_t)(bb[e] >> 32);
-      mn = min(mn, h);
-      mx = max(mx, h);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    long long lo = (long long)mn - 1, hi = mx;  // count(<= hi) >= S > count(<= lo)
-    while (hi - lo > 1) {
-      const uint32_t mid = (uint32_t)(lo + ((hi - lo) >> 1));
-      const int c = sl_count(bb, n, mid, false, 0xffffffffll);
-      if (c >= S) {
-        hi = mid;
-        if (c <= S + 32) break;
-      } else {
-        lo = mid;
-      }
-    }
-    const uint32_t v = (uint32_t)hi;
+    // keep at most half of the room above S, so that the next cut is some flushes away
+    const uint32_t v = sl_cut_value(bb, n, S, S + (BBC - KW - S) / 2);
     unsigned long long nt = ((unsigned long long)v << 32) | 0xffffffffull;
     if (sl_count(bb, n, v, false, 0xffffffffll) > BBC - KW) {
       // a tie group at v: the exact S-th composite, bisecting the positions at v
