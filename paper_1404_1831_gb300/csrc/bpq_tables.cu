@@ -83,57 +83,83 @@ __global__ void __launch_bounds__(128) tc_table_kernel(const float* __restrict__
   // multiple of 16): the BF16 value, and with `split` the next two planes
   const bool vec4 = ((pr.dim | lda | pr.a_off) & 3) == 0;
   const int q4 = kpad >> 2;
-  for (int e = tid; e < TC_M * q4; e += 128) {
-    const int r = e / q4, k = (e - r * q4) << 2;
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
-    if (a0 + r < na) {
-      const float* src = A + (int64_t)(a0 + r) * lda + pr.a_off + k;
-      if (vec4) {
-        if (k < pr.dim) {
-          const float4 f = *reinterpret_cast<const float4*>(src);
-          v[0] = f.x;
-          v[1] = f.y;
-          v[2] = f.z;
-          v[3] = f.w;
-        }
-      } else {
+  auto pack = [](const __nv_bfloat16* b) {
+    uint2 pk;
+    pk.x = (uint32_t)__bfloat16_as_ushort(b[0]) | ((uint32_t)__bfloat16_as_ushort(b[1]) << 16);
+    pk.y = (uint32_t)__bfloat16_as_ushort(b[2]) | ((uint32_t)__bfloat16_as_ushort(b[3]) << 16);
+    return pk;
+  };
+  // four steps' loads are issued before any of them is converted and stored
+  constexpr int GL = 4;
+  for (int e0 = tid; e0 < TC_M * q4; e0 += 128 * GL) {
+    float v[GL][4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = k + j < pr.dim ? src[j] : 0.f;
+    for (int g = 0; g < GL; ++g) {
+      const int e = e0 + g * 128;
+      const int r = e / q4, k = (e - r * q4) << 2;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[g][j] = 0.f;
+      if (e < TC_M * q4 && a0 + r < na) {
+        const float* src = A + (int64_t)(a0 + r) * lda + pr.a_off + k;
+        if (vec4) {
+          if (k < pr.dim) {
+            const float4 f = *reinterpret_cast<const float4*>(src);
+            v[g][0] = f.x;
+            v[g][1] = f.y;
+            v[g][2] = f.z;
+            v[g][3] = f.w;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) v[g][j] = k + j < pr.dim ? src[j] : 0.f;
+        }
       }
     }
-    __nv_bfloat16 b1[4], b2[4], b3[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      b1[j] = __float2bfloat16_rn(v[j]);
-      const float r1 = __fsub_rn(v[j], __bfloat162float(b1[j]));
-      bad |= r1 != 0.f;
-      b2[j] = __float2bfloat16_rn(r1);
-      b3[j] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(b2[j])));
-    }
-    auto pack = [](const __nv_bfloat16* b) {
-      uint2 pk;
-      pk.x = (uint32_t)__bfloat16_as_ushort(b[0]) | ((uint32_t)__bfloat16_as_ushort(b[1]) << 16);
-      pk.y = (uint32_t)__bfloat16_as_ushort(b[2]) | ((uint32_t)__bfloat16_as_ushort(b[3]) << 16);
-      return pk;
-    };
-    *reinterpret_cast<uint2*>(sA + core_off(r, k, KB)) = pack(b1);
-    if (split) {
-      *reinterpret_cast<uint2*>(sA2 + core_off(r, k, KB)) = pack(b2);
-      *reinterpret_cast<uint2*>(sA3 + core_off(r, k, KB)) = pack(b3);
+    for (int g = 0; g < GL; ++g) {
+      const int e = e0 + g * 128;
+      if (e >= TC_M * q4) break;
+      const int r = e / q4, k = (e - r * q4) << 2;
+      __nv_bfloat16 b1[4], b2[4], b3[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        b1[j] = __float2bfloat16_rn(v[g][j]);
+        const float r1 = __fsub_rn(v[g][j], __bfloat162float(b1[j]));
+        bad |= r1 != 0.f;
+        b2[j] = __float2bfloat16_rn(r1);
+        b3[j] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(b2[j])));
+      }
+      *reinterpret_cast<uint2*>(sA + core_off(r, k, KB)) = pack(b1);
+      if (split) {
+        *reinterpret_cast<uint2*>(sA2 + core_off(r, k, KB)) = pack(b2);
+        *reinterpret_cast<uint2*>(sA3 + core_off(r, k, KB)) = pack(b3);
+      }
     }
   }
   const int bpl = (pr.b_planes == 2 && !bsplit) ? 0 : pr.b_planes;  // a second plane needs its smem
   {  // codewords: one 16-byte core row per step (and the second plane)
     const int q8 = kpad >> 3;
-    for (int e = tid; e < nt * q8; e += 128) {
-      const int r = e / q8, k = (e - r * q8) << 3;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u), v2 = make_uint4(0u, 0u, 0u, 0u);
-      if (n0 + r < pr.nb) {
-        v = *reinterpret_cast<const uint4*>(pr.Bb + (int64_t)(n0 + r) * kpad + k);
-        if (bpl == 2) v2 = *reinterpret_cast<const uint4*>(pr.Bb2 + (int64_t)(n0 + r) * kpad + k);
+    for (int e0 = tid; e0 < nt * q8; e0 += 128 * GL) {
+      uint4 v[GL], v2[GL];
+#pragma unroll
+      for (int g = 0; g < GL; ++g) {
+        const int e = e0 + g * 128;
+        const int r = e / q8, k = (e - r * q8) << 3;
+        v[g] = make_uint4(0u, 0u, 0u, 0u);
+        v2[g] = make_uint4(0u, 0u, 0u, 0u);
+        if (e < nt * q8 && n0 + r < pr.nb) {
+          v[g] = *reinterpret_cast<const uint4*>(pr.Bb + (int64_t)(n0 + r) * kpad + k);
+          if (bpl == 2) v2[g] = *reinterpret_cast<const uint4*>(pr.Bb2 + (int64_t)(n0 + r) * kpad + k);
+        }
       }
-      *reinterpret_cast<uint4*>(sB + core_off(r, k, KB)) = v;
-      if (bpl == 2) *reinterpret_cast<uint4*>(sB2 + core_off(r, k, KB)) = v2;
+#pragma unroll
+      for (int g = 0; g < GL; ++g) {
+        const int e = e0 + g * 128;
+        if (e >= nt * q8) break;
+        const int r = e / q8, k = (e - r * q8) << 3;
+        *reinterpret_cast<uint4*>(sB + core_off(r, k, KB)) = v[g];
+        if (bpl == 2) *reinterpret_cast<uint4*>(sB2 + core_off(r, k, KB)) = v2[g];
+      }
     }
   }
   for (int c = tid; c < nt; c += 128) bn_s[c] = n0 + c < pr.nb ? pr.bn[n0 + c] : 0.f;

@@ -800,7 +800,7 @@ __global__ void __launch_bounds__(NT, 4) traverse_kernel(TraverseArgs a, int onl
 //    compacted.  Every cell outside this row x column grid has a key of at least
 //    the limit min(min(d1) + theta2, theta1 + min(d2)), so bands stay below it;
 //    when the budget is not reached below the limit the grid is rebuilt larger
-//    (rows keep their progress, kept per row id);
+//    (rows keep their progress: the old grid's rows are among the new ones);
 //  * each band holds at most BCAP cells: its edge is searched with warp-wide
 //    counts and its cells are enumerated.  The band that reaches the budget is
 //    sorted by (key, cell id) in registers and cut there; earlier bands are
@@ -822,7 +822,7 @@ struct WarpSmem {
   uint16_t cp2[PCAP];
   uint16_t rid[RCAP];
   uint16_t rvhi[RCAP];
-  uint16_t vloid[WARP_TMAX];  // columns already visited, per row id
+  uint16_t vlo[RCAP];   // columns already visited, per grid row
 };
 
 __device__ __forceinline__ uint32_t warp_min_u32(uint32_t x) {
@@ -847,8 +847,14 @@ __device__ __forceinline__ V warp_excl_scan(V x, V* total) {
 // Builds the row x column grid for about `want` rows and columns.  Returns false
 // if it would exceed the caps.
 __device__ __noinline__ bool build_grid(WarpSmem& W, const float* d1, const float* d2, int T, int TP, float want,
-                                        float min1, float min2, int* P2out, int* Rout, uint32_t* limit) {
+                                        float min1, float min2, int Rold, int* P2out, int* Rout, uint32_t* limit) {
   const int lane = threadIdx.x & 31;
+  // a rebuild keeps the progress of the previous grid's rows: their (row id,
+  // visited columns) go to rfk (rewritten below), sorted by row id.  The new
+  // thresholds are not lower, so the old rows are among the new ones and the old
+  // sorted columns stay a prefix of the new ones.
+  for (int r = lane; r < Rold; r += 32) W.rfk[r] = ((uint32_t)W.rid[r] << 16) | W.vlo[r];
+  __syncwarp();
   uint32_t th1 = ORD_INF, th2 = ORD_INF;
   if (T > PCAP) {  // thresholds: a quantile of 64 sampled rows / columns each
     const int stride = TP / 64;
@@ -909,8 +915,18 @@ __device__ __noinline__ bool build_grid(WarpSmem& W, const float* d1, const floa
     W.cp2[v] = (uint16_t)(uint32_t)e;
   }
   __syncwarp();
+  for (int r = lane; r < R; r += 32) {  // each new row's progress: a search of the old rows
+    const uint32_t id = W.rid[r];
+    int lo = 0, hi = Rold;  // first old row with id >= this one
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((W.rfk[mid] >> 16) < id) lo = mid + 1; else hi = mid;
+    }
+    W.vlo[r] = (lo < Rold && (W.rfk[lo] >> 16) == id) ? (uint16_t)(W.rfk[lo] & 0xffffu) : (uint16_t)0;
+  }
+  __syncwarp();
   for (int r = lane; r < R; r += 32) {
-    const int v = W.vloid[W.rid[r]];
+    const int v = W.vlo[r];
     W.rfk[r] = v < P2 ? f2ord(__fadd_rn(W.rs1[r], W.cs2[v])) : ORD_INF;
   }
   __syncwarp();
@@ -930,7 +946,7 @@ __device__ __forceinline__ void hand_over(const TraverseArgs& a, int64_t q) {
   }
 }
 
-__global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs a) {
+__global__ void __launch_bounds__(WPB * 32, 7) traverse_warp_kernel(TraverseArgs a) {
   __shared__ WarpSmem smw[WPB];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpSmem& W = smw[warp];
@@ -958,12 +974,11 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
     for (int t = lane; t < T; t += 32) {
       m1 = min(m1, f2ord(__ldg(d1 + t)));
       m2 = min(m2, f2ord(__ldg(d2 + t)));
-      W.vloid[t] = 0;
     }
     const float min1 = ord2f(warp_min_u32(m1)), min2 = ord2f(warp_min_u32(m2));
     int P2 = 0, R = 0;
     uint32_t limit = ORD_INF;
-    bool fb = !build_grid(W, d1, d2, T, TP, want, min1, min2, &P2, &R, &limit);
+    bool fb = !build_grid(W, d1, d2, T, TP, want, min1, min2, 0, &P2, &R, &limit);
     long long committed = 0;
     int nout = 0;
     bool overflow = false;
@@ -985,7 +1000,7 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
           break;
         }
         want = fminf(want_max, 2.f * want);
-        fb = !build_grid(W, d1, d2, T, TP, want, min1, min2, &P2, &R, &limit);
+        fb = !build_grid(W, d1, d2, T, TP, want, min1, min2, R, &P2, &R, &limit);
         continue;
       }
       const int rh = (int)(uint32_t)fm;
@@ -999,13 +1014,13 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
       uint16_t* Hp = Lp + RCAP;
       uint16_t* Tp = Hp + RCAP;
       for (int r = lane; r < R; r += 32) {
-        Lp[r] = W.vloid[W.rid[r]];
+        Lp[r] = W.vlo[r];
         Hp[r] = (uint16_t)P2;
       }
       auto count = [&](uint32_t h) -> long long {  // per-row results go to Tp
         long long c = 0;
         for (int r = lane; r < R; r += 32) {
-          const int v = W.vloid[W.rid[r]];
+          const int v = W.vlo[r];
           int e = v;
           if (W.rfk[r] <= h) e = row_count(W.cs2, Hp[r], W.rs1[r], max((int)Lp[r], v + 1), h);
           Tp[r] = (uint16_t)e;
@@ -1024,7 +1039,7 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
         Tp = t;
       };
       const uint32_t lim1 = limit == ORD_INF ? ORD_INF - 1 : limit - 1;
-      const int vh = W.vloid[W.rid[rh]];
+      const int vh = W.vlo[rh];
       const float sh = W.rs1[rh];
       const uint32_t g_hi = min(lim1, f2ord(__fadd_rn(sh, W.cs2[min(P2 - 1, vh + BCAP)])));
       const uint32_t g1 = min(g_hi, f2ord(__fadd_rn(sh, W.cs2[min(P2 - 1, vh + 16)])));
@@ -1081,7 +1096,7 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
       // the band's cells: columns [vlo, Lp) of every row
       int loc = 0;
       for (int r = lane; r < R; r += 32) {
-        const int v = W.vloid[W.rid[r]];
+        const int v = W.vlo[r];
         const int vhi = Lp[r];
         W.rvhi[r] = (uint16_t)vhi;
         loc += vhi - v;
@@ -1090,7 +1105,7 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
       int E;
       int pos = warp_excl_scan(loc, &E);
       for (int r = lane; r < R; r += 32) {
-        const int v0 = W.vloid[W.rid[r]], v1 = W.rvhi[r];
+        const int v0 = W.vlo[r], v1 = W.rvhi[r];
         const uint32_t rowbase = (uint32_t)W.rid[r] * (uint32_t)T;
         const float s1r = W.rs1[r];
         for (int v = v0; v < v1; ++v)
@@ -1184,7 +1199,7 @@ __global__ void __launch_bounds__(WPB * 32, 6) traverse_warp_kernel(TraverseArgs
       __syncwarp();
       for (int r = lane; r < R; r += 32) {
         const int v = W.rvhi[r];
-        W.vloid[W.rid[r]] = (uint16_t)v;
+        W.vlo[r] = (uint16_t)v;
         W.rfk[r] = v < P2 ? f2ord(__fadd_rn(W.rs1[r], W.cs2[v])) : ORD_INF;
       }
       __syncwarp();

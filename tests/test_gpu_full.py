@@ -138,3 +138,23 @@ def test_full_overlapped_passes_equal_separate_calls(full, L):
     ids2, dists2 = ix.scan(q, lut, cells, ncells, 100, "fbpq")
     assert np.array_equal(ids.cpu().numpy(), ids2.cpu().numpy())
     assert np.array_equal(dists.cpu().numpy(), dists2.cpu().numpy())
+
+
+def test_full_traversal_all_queries(full):
+    """Every query of the 10k batch, not a sample: the warp pass (with its grid rebuilds) and
+    the CTA pass emit exactly the multi-sequence order's non-empty cells and L' (§2.3.3)."""
+    import synthdata as sd
+    from oracle import bpq_oracle as O
+    from tests.parity import cells_from_gpu
+    index = full["index"]
+    counts = index.lists.counts()
+    L = 10_000
+    cap = int(min(L, (counts > 0).sum()))
+    cells, ncells, npoints = full["ix"].traverse(full["q"], L, cap)
+    got = cells_from_gpu(cells.cpu().numpy(), ncells.cpu().numpy())
+    npoints = npoints.cpu().numpy()
+    qh = sd.points(full["mix"], sd.STREAM_QUERY, 0, full["w"].n_query)
+    for n in range(len(qh)):
+        d1, d2 = O.coarse_distances(qh[n], index.cb)
+        oc, _, total = O.traverse_multisequence(d1, d2, counts, L)
+        assert np.array_equal(got[n][0], oc[counts[oc] > 0]) and npoints[n] == total, n
