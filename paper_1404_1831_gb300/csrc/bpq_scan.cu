@@ -1039,9 +1039,10 @@ __global__ void __launch_bounds__(NT, HB ? 5 : 8) fbpq_scan_seg_kernel(ScanArgs 
             for (int u = 0; u < U; ++u) {
               const int i = c + 1 + 32 * u + lane;
               const int o = (i <= nch ? c_pref[i] : 0x7fffffff) - f;  // >= 1 + 32u
+              const int hh = o >> 5;  // the window half the boundary falls in (>= U: none)
+              const unsigned bit = 1u << (o & 31);
 #pragma unroll
-              for (int h = u; h < U; ++h)
-                if (o >= 32 * h && o < 32 * h + 32) bits[h] |= 1u << (o - 32 * h);
+              for (int h = u; h < U; ++h) bits[h] |= (hh == h) ? bit : 0u;
             }
             int below = c;
 #pragma unroll
