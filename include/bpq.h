@@ -257,6 +257,13 @@ int bpq_traverse(const bpq_index* idx, const float* queries_dev, int64_t nq, con
  *  query must fit, else BPQ_ECAPACITY).
  * Asynchronous on stream; per-query failures of a fixed-size buffer (a cell tie
  * group larger than the traversal band) are reported by bpq_search_status.
+ * With the FBPQ scorer and k <= 128, part of the work (the PQ table, and the
+ * traversal and scan of the queries the common traversal path hands over) runs
+ * on a second stream that joins `stream` before the call's work on it ends; that
+ * stream and its events are created, per device and caller stream, on the first
+ * such call outside a stream capture (a call under capture that finds none runs
+ * everything on `stream`) and are kept until the process exits (they do not
+ * survive cudaDeviceReset).
  */
 int bpq_search(const bpq_index* idx, const float* queries_dev, int64_t nq, const int64_t* L_host,
                int64_t L_stride, int32_t k, int32_t scorer, int32_t* ids_dev, float* dists_dev,
