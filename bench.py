@@ -180,13 +180,16 @@ def oracle_sample_text(w, L, n, own=True):
 # ---------------------------------------------------------------------------
 # GPU side
 # ---------------------------------------------------------------------------
-def launches_per_step(w, scorer):
+def launches_per_step(w, scorer, k=100):
     """Kernels one search launches: the query tables (one more for the LUT of the
     table-based scorers), the traversal (its common path and the fallback pass
-    when T <= 1024) and the scan."""
+    when T <= 1024) and the scan (twice for the FBPQ per-point scorer with k <= 128
+    and T <= 1024: the queries the common traversal path finished, and on the
+    second stream the ones it handed over)."""
     tables = 2 if scorer in ("fbpq", "fbpq_tables") else 1
     traverse = 2 if w.T <= 1024 else 1
-    return tables + traverse + 1
+    scans = 2 if (scorer == "fbpq" and k <= 128 and w.T <= 1024) else 1
+    return tables + traverse + scans
 
 
 class ClockSampler:
@@ -456,7 +459,7 @@ def run_ours(args):
                       f"iterations on {w.n_learn} learn points", "l2": "flushed between steps (512 MB write)",
                       "parallelism": f"replicas x{world} (independent query batches)"},
            "roofline": roof, "roofline_other": roof_trav if scan_dominant else roof_scan,
-           "gpu_launches": launches_per_step(w, scorer) * args.steps, "clocks": clocks,
+           "gpu_launches": launches_per_step(w, scorer, k) * args.steps, "clocks": clocks,
            "phases_ms": ph, "candidates_per_step": cand, "visited_cells_per_step": ncell_total,
            "index": {"n_points": info.n_points, "n_nonempty_cells": info.n_nonempty, "max_cell": info.max_cell},
            "e2e": e2e, "setup_s": round(setup_s, 1)}
