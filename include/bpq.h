@@ -149,6 +149,11 @@ int bpq_create(bpq_index** out, const bpq_params* p, const float* C1_host, const
  *  [-2^20, 2^20] (K-means sums are exact int64 and every centroid is the mean
  *  rounded half up to an integer); n_learn >= max(T, 256).  K-means starts from
  *  the first T (or 256) learn vectors; local codebooks start from the global ones.
+ *  Real-valued data: train on round(x * s) for a scale s of your choice, and add
+ *  and search vectors scaled the same way (searches then report distances times
+ *  s^2); or build the index from your own codebooks with bpq_create, which takes
+ *  real-valued codebooks.  Queries and added points may be real-valued either way
+ *  (query tiles that BF16 cannot hold exactly are tabulated in FP32).
  *  Synchronizes the stream before returning.
  *  Otherwise loads path (written by bpq_save) onto `device`.
  * Errors: BPQ_EINVAL (bad params, non-integer data), BPQ_EIO, BPQ_ECORRUPT,

@@ -158,3 +158,21 @@ def test_full_traversal_all_queries(full):
         d1, d2 = O.coarse_distances(qh[n], index.cb)
         oc, _, total = O.traverse_multisequence(d1, d2, counts, L)
         assert np.array_equal(got[n][0], oc[counts[oc] > 0]) and npoints[n] == total, n
+
+
+def test_full_search_all_queries(full):
+    """Every query of the 10k batch at L = 10k (the benchmark's launch): the GPU's top-100 ids
+    and distances equal the oracle's (multi-sequence traversal, FP64 FBPQ distances), so
+    recall@1/10/100 against any ground truth is identical too."""
+    import synthdata as sd
+    from oracle import bpq_oracle as O
+    L, k = 10_000, 100
+    ids, dists = full["ix"].search(full["q"], L, k, "fbpq")
+    full["ix"].search_status()
+    ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+    qh = sd.points(full["mix"], sd.STREAM_QUERY, 0, full["w"].n_query)
+    exact = 0
+    for n in range(len(qh)):
+        o_ids, o_d, _, _ = O.search_one(full["index"], qh[n], L, k, "fbpq")
+        exact += assert_topk_match(ids[n:n + 1], dists[n:n + 1], o_ids[None], o_d[None])
+    assert exact == len(qh)
