@@ -103,3 +103,34 @@ def test_global_counts_are_checked(shards):
     ix.set_global_counts(sum(p.cell_counts() for p in parts))
     shard = ix.search(q, 10_000, 10, "fbpq")[0]
     assert not torch.equal(alone, shard)
+
+
+@pytest.mark.parametrize("scorer", ["hbpq", "hbpq_recon"])
+def test_hbpq_shards_merge_to_the_whole_index_answer(tiny_oracle, scorer):
+    """HBPQ (local codebooks, §3.2) on point shards: the per-half-cell tables are built for the
+    cells every shard visits with the whole index's counts; merged = the whole index's lists."""
+    import paper_1404_1831_gb300 as bpq
+    from oracle import bpq_oracle as O
+    t = tiny_oracle
+    cbl = O.train_hbpq_local(t["learn"], t["cb"], t["w"].kmeans_iters)
+    base = t["base"]
+    n = len(base)
+
+    def make(lo, cnt):
+        ix = bpq.Index.create(cbl.C1, cbl.C2, cbl.R, Q=cbl.Q, S=cbl.S)
+        ix.add(torch.as_tensor(base[lo:lo + cnt], dtype=torch.float32, device=DEV),
+               ids=torch.arange(lo, lo + cnt, dtype=torch.int32, device=DEV))
+        ix.finalize()
+        return ix
+
+    full = make(0, n)
+    parts = [make(*multi.shard_points(n, r, 2)) for r in range(2)]
+    counts = sum(ix.cell_counts() for ix in parts)
+    for ix in parts:
+        ix.set_global_counts(counts)
+    q = torch.as_tensor(t["queries"], dtype=torch.float32, device=DEV)
+    k = 50
+    a_i, a_d = [x.cpu().numpy() for x in full.search(q, 5_000, k, scorer)]
+    m_i, m_d = _merged(parts, lambda ix: ix.search(q, 5_000, k, scorer), k)
+    assert np.array_equal(a_i, m_i)
+    assert np.array_equal(a_d.astype(np.float64), m_d)
