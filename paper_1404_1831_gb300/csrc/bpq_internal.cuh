@@ -8,6 +8,7 @@
 #include <map>
 #include <stdexcept>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/bpq.h"
@@ -123,11 +124,16 @@ __device__ __forceinline__ void warp_hist_add_w(unsigned long long* hist, uint32
   if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&hist[bin], (unsigned long long)lo + ((unsigned long long)hi << 16));
 }
 
+// Sum over the warp: one redux.sync for 32-bit integers, shuffles otherwise.
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
+  if constexpr (std::is_same<T, int>::value || std::is_same<T, unsigned>::value) {
+    return __reduce_add_sync(0xffffffffu, v);
+  } else {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  }
 }
 
 // ---------------------------------------------------------------------------

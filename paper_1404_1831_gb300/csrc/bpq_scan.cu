@@ -535,11 +535,8 @@ __device__ uint32_t warp_cut(const uint64_t* wb, int n, int k) {
       mx = max(mx, h[i]);
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  }
+  mn = __reduce_min_sync(0xffffffffu, mn);
+  mx = __reduce_max_sync(0xffffffffu, mx);
   // count(<= hi) >= k; count(<= lo) < k (lo = mn - 1 as a 64-bit value)
   long long lo = (long long)mn - 1, hi = mx;
   while (hi - lo > 1) {
@@ -648,11 +645,8 @@ __device__ uint32_t block_cut(const uint64_t* a, int n, int k, int* red) {
       mx = max(mx, h[i]);
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  }
+  mn = __reduce_min_sync(0xffffffffu, mn);
+  mx = __reduce_max_sync(0xffffffffu, mx);
   if (lane == 0) {
     red[w] = (int)mn;
     red[NW + w] = (int)mx;
@@ -786,15 +780,13 @@ __device__ __noinline__ uint32_t sl_cut_value(const uint64_t* bb, int n, int S, 
   if (cg < S) {
     uint32_t mx = 0u;
     for (int e = lane; e < n; e += 32) mx = max(mx, (uint32_t)(bb[e] >> 32));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mx = __reduce_max_sync(0xffffffffu, mx);
     lo = g;
     hi = mx;
   } else {
     uint32_t mn = 0xffffffffu;
     for (int e = lane; e < n; e += 32) mn = min(mn, (uint32_t)(bb[e] >> 32));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mn = __reduce_min_sync(0xffffffffu, mn);
     lo = (long long)mn - 1;
     hi = g;
   }

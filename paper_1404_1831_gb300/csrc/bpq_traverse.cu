@@ -825,11 +825,7 @@ struct WarpSmem {
   uint16_t vlo[RCAP];   // columns already visited, per grid row
 };
 
-__device__ __forceinline__ uint32_t warp_min_u32(uint32_t x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
-  return x;
-}
+__device__ __forceinline__ uint32_t warp_min_u32(uint32_t x) { return __reduce_min_sync(0xffffffffu, x); }
 
 template <typename V>
 __device__ __forceinline__ V warp_excl_scan(V x, V* total) {
@@ -1018,7 +1014,7 @@ __global__ void __launch_bounds__(WPB * 32, 7) traverse_warp_kernel(TraverseArgs
         Hp[r] = (uint16_t)P2;
       }
       auto count = [&](uint32_t h) -> long long {  // per-row results go to Tp
-        long long c = 0;
+        int c = 0;  // at most RCAP x PCAP cells
         for (int r = lane; r < R; r += 32) {
           const int v = W.vlo[r];
           int e = v;
@@ -1026,7 +1022,7 @@ __global__ void __launch_bounds__(WPB * 32, 7) traverse_warp_kernel(TraverseArgs
           Tp[r] = (uint16_t)e;
           c += e - v;
         }
-        return warp_sum(c);
+        return (long long)warp_sum(c);
       };
       auto take_lo = [&]() {
         uint16_t* t = Lp;
