@@ -524,14 +524,17 @@ def serve_block(ix, w, mix, k, seconds, seed=11, n_max=300_000, max_batch=4096, 
     qh = sdev.points_cuda(mix, sd.STREAM_QUERY, w.n_query, n_max).cpu().numpy()  # after the timed batch
     mix_L = np.array([1_000, 10_000, 100_000], dtype=np.int64)
     Ls = mix_L[np.random.default_rng(seed).integers(0, len(mix_L), n_max)]
-    n_sat = min(n_max, 60_000)
+    n_sat = min(n_max, 120_000)
     # scan schedule per batch class the server will form (budget class x batch size), by measurement
     qd = torch.as_tensor(qh[:max_batch], device="cuda")
     tuned = {f"L{int(Lc)}_n{nb}": ix.autotune(qd[:nb], int(Lc), k)
              for Lc in mix_L for nb in (32, 128, 512, 2048)}
     cfg = dict(k=k, slots=slots, max_batch=max_batch, L_max=int(mix_L.max()), device_bytes=device_bytes)
     serving.serve_continuous(ix, qh[:4096], Ls[:4096], np.zeros(4096), **cfg)  # warm-up
-    sat = serving.serve_continuous(ix, qh[:n_sat], Ls[:n_sat], np.zeros(n_sat), **cfg)
+    # saturated rate: every query queued at time zero; the better of two passes (a pass lasts tens of
+    # milliseconds, so one host-side hiccup would otherwise set the offered loads below)
+    sat = min((serving.serve_continuous(ix, qh[:n_sat], Ls[:n_sat], np.zeros(n_sat), **cfg) for _ in range(2)),
+              key=lambda r: r.wall_s)
     sat_qps = n_sat / sat.wall_s
     sat_queue = serving.saturated_qps(ix, qh, Ls, k, batch=max_batch)
     out = {"L_mix": mix_L.tolist(), "k": k, "latency": "arrival to results in host memory (copies included)",
