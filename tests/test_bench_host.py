@@ -32,3 +32,20 @@ def test_recorded_counters_match_the_current_kernels():
         rec = b.recorded_traffic(f)
         assert rec is None or rec["source_sha256_16"] == b.source_digest(
             os.path.join(ROOT, "paper_1404_1831_gb300", "csrc", f))
+
+
+def test_launch_claim_counts_every_kernel_of_a_search():
+    """The bench's gpu_launches claim: two table kernels (coarse and PQ) for the FBPQ scorers, the
+    traversal's two passes at T <= 1024, and two scan launches for the FBPQ per-point scorer with
+    k <= 128 (the finished queries, and on the second stream the handed-over ones)."""
+    import dataclasses
+
+    import synthdata as sd
+    b = _bench()
+    w = sd.SIFT10M
+    assert b.launches_per_step(w, "fbpq", 100) == 6
+    assert b.launches_per_step(w, "fbpq", 1000) == 5
+    assert b.launches_per_step(w, "fbpq_tables", 100) == 5
+    assert b.launches_per_step(w, "recon", 100) == 4
+    big_T = dataclasses.replace(w, T=2048)
+    assert b.launches_per_step(big_T, "fbpq", 100) == 4
